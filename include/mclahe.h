@@ -1,0 +1,224 @@
+/*
+ * mclahe.h -- C ABI of the GB300 (sm_103a) implementation of Multidimensional
+ * Contrast Limited Adaptive Histogram Equalization (MCLAHE; Stimper, Bauer,
+ * Ernstorfer, Schoelkopf, Xian, arXiv:1906.11355).
+ *
+ * The operation (Algorithm 1 of the paper):
+ *   1. pad the D-dimensional volume symmetrically so that it splits into whole
+ *      kernels of size b and every voxel has 2^D neighbouring kernels
+ *      (Sec. III.B, Eq. (1)-(2));
+ *   2. build one n_bins histogram per kernel, over a global or a per-kernel
+ *      adaptive intensity range (Algorithm 1; Sec. III.D);
+ *   3. clip each histogram at the clip limit, redistribute the excess equally,
+ *      and turn its CDF, normalised by its min and max, into the kernel's
+ *      mapping table (Algorithm 1);
+ *   4. map every voxel by the multilinear (Lagrange) interpolation of its 2^D
+ *      neighbouring kernels' tables at the voxel's bin (Sec. III.C,
+ *      Eq. (12)-(13)).
+ *
+ * Conventions shared by every entry point
+ *   - Volumes are float32, C order (dimension 0 slowest, D-1 contiguous),
+ *     1 <= D <= 4, every extent >= 1, and the device pointers are 16-byte
+ *     aligned.  Intensities must be finite.
+ *   - The caller owns every device buffer and the stream.  The library owns
+ *     only host-side plan objects; it never allocates device memory.
+ *   - No entry point synchronises the stream unless it says so.  Argument
+ *     errors are returned synchronously and leave the device untouched.
+ *     A failed kernel launch returns MCLAHE_ERR_CUDA.  Errors found by device
+ *     code are written to the status word at the start of the workspace and
+ *     are read back by mclahe_sync_status().
+ *   - Readings of points the paper leaves open:
+ *       padding length p = 2b - 1 - ((s - 1) mod b) (Eq. (1); Algorithm 1's
+ *         first step prints "+", which cannot make s + p a multiple of b);
+ *       symmetric padding = edge-inclusive mirror, which needs b <= s;
+ *       bin quantiser: scale = n_bins / (hi - lo) in fp32 (0 if hi <= lo),
+ *         bin = clamp(floor((x - lo) * scale), 0, n_bins - 1), each operation
+ *         rounded to nearest in fp32;
+ *       global range = [min, max] of the input unless given;
+ *       clip threshold T = clip_limit * V, V = prod(b) voxels per kernel;
+ *       excess E = sum over bins of max(h - T, 0), added as E / n_bins to
+ *         every bin (one pass);
+ *       kernel centre along dim j = k * b_j + (b_j - 1) / 2 in padded
+ *         coordinates; a voxel at original index x sits at x + p_j0;
+ *       a kernel whose CDF is constant gets the all-zero table;
+ *       the output lies in [0, 1] and is not rescaled to the input range.
+ */
+#ifndef MCLAHE_H
+#define MCLAHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(MCLAHE_BUILD) && defined(__GNUC__)
+#define MCLAHE_API __attribute__((visibility("default")))
+#else
+#define MCLAHE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-compatible with cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *mclahe_stream_t;
+
+/* Opaque host-side plan (geometry, parameters, launch shapes). */
+typedef struct mclahe_plan_s *mclahe_plan_t;
+
+typedef enum {
+    MCLAHE_OK = 0,
+    MCLAHE_ERR_INVALID_ARG = 1,   /* bad shape, kernel size, bins, clip, pointer */
+    MCLAHE_ERR_UNSUPPORTED = 2,   /* valid in the paper, outside this build's limits */
+    MCLAHE_ERR_WORKSPACE = 3,     /* workspace missing, too small or misaligned */
+    MCLAHE_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed */
+    MCLAHE_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    MCLAHE_ERR_NO_MEMORY = 6,     /* host allocation failed */
+    MCLAHE_ERR_DEVICE = 7         /* device code recorded an internal error */
+} mclahe_status;
+
+typedef enum {
+    MCLAHE_RANGE_GLOBAL = 0,      /* one histogram range for all kernels (GHR) */
+    MCLAHE_RANGE_ADAPTIVE = 1     /* each kernel's own [min, max] (AHR, Sec. III.D) */
+} mclahe_range_mode;
+
+/* Geometry and workspace layout of a plan (filled by mclahe_plan_query). */
+typedef struct {
+    int32_t ndim;
+    int32_t n_bins;
+    int32_t mode;                 /* mclahe_range_mode */
+    float clip_limit;
+    int64_t shape[4];             /* s */
+    int64_t kernel_size[4];       /* b */
+    int64_t pad[4];               /* p, Eq. (1) */
+    int64_t pad_before[4];        /* p0 = p // 2, Eq. (2) */
+    int64_t pad_after[4];         /* p1 = (p + 1) // 2, Eq. (2) */
+    int64_t n_kernels_dim[4];     /* n = (s + p) / b */
+    int64_t n_kernels;            /* K = prod(n) */
+    int64_t kernel_voxels;        /* V = prod(b) */
+    int64_t n_voxels;             /* prod(s) */
+    /* byte offsets inside the workspace (all 256-byte aligned) */
+    size_t ws_status;             /* uint32 status word */
+    size_t ws_range_keys;         /* uint32 [2 or 2K] order-preserving min/max keys */
+    size_t ws_hist;               /* uint32 [K][n_bins] kernel histograms */
+    size_t ws_lo;                 /* float  [K] histogram range start per kernel */
+    size_t ws_scale;              /* float  [K] histogram scale per kernel */
+    size_t ws_lut;                /* float  [K][n_bins] mapping tables */
+    size_t ws_scratch;            /* backward partials */
+    size_t ws_bytes;              /* total workspace size */
+} mclahe_plan_info;
+
+/*
+ * mclahe_plan -- validate parameters and build a plan (host only; no CUDA call).
+ * Paper: Algorithm 1 (inputs data_in; parameters kernel_size, clip_limit in
+ * [0, 1], n_bins), Sec. III.B (padding geometry), Sec. III.D (range mode).
+ *   out          receives the plan; release it with mclahe_plan_destroy.
+ *   ndim         D, 1..4.
+ *   shape        D extents s_i >= 1.
+ *   kernel_size  D kernel extents, 1 <= b_i <= s_i (the mirror padding of
+ *                Sec. III.B reflects at most once).
+ *   n_bins       2..4096.
+ *   clip_limit   [0, 1]; the forward pass may override it per call.
+ *   mode         MCLAHE_RANGE_GLOBAL or MCLAHE_RANGE_ADAPTIVE.
+ *   global_range nullable {lo, hi}; GHR only.  NULL: the input's min and max,
+ *                found on the device by every forward call.
+ * Returns MCLAHE_OK, MCLAHE_ERR_INVALID_ARG, MCLAHE_ERR_UNSUPPORTED (volume or
+ * kernel too large for 32-bit counters), MCLAHE_ERR_NO_MEMORY.
+ */
+MCLAHE_API mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
+                          const int32_t *kernel_size, int32_t n_bins, float clip_limit,
+                          mclahe_range_mode mode, const float *global_range);
+
+/* Release a plan (NULL is ignored). */
+MCLAHE_API void mclahe_plan_destroy(mclahe_plan_t plan);
+
+/* Fill *info with the plan's geometry and workspace layout. */
+MCLAHE_API mclahe_status mclahe_plan_query(mclahe_plan_t plan, mclahe_plan_info *info);
+
+/* Bytes of device workspace one forward/backward call of this plan needs
+ * (0 for a NULL plan).  The caller allocates it, 256-byte aligned. */
+MCLAHE_API size_t mclahe_workspace_bytes(mclahe_plan_t plan);
+
+/*
+ * mclahe_forward -- the whole of Algorithm 1 on one volume, on `stream`.
+ * Paper: Algorithm 1; Sec. III.B-III.D; Eq. (1)-(3), (12)-(13).
+ *   d_in      device, prod(shape) float32, read only.
+ *   d_out     device, prod(shape) float32, written; must not alias d_in.
+ *   d_ws      device workspace of ws_bytes >= mclahe_workspace_bytes(plan).
+ *             On return (in stream order) it holds the range, the kernel
+ *             histograms and the mapping tables at the offsets of
+ *             mclahe_plan_info; mclahe_backward reads them.
+ *   d_clip    nullable device float: clip limit for this call (overrides the
+ *             plan's; read on the device, so it can be a learnable parameter).
+ *             Values outside [0, 1] are clamped.
+ * Returns MCLAHE_OK, MCLAHE_ERR_INVALID_ARG (NULL or misaligned pointers),
+ * MCLAHE_ERR_WORKSPACE, MCLAHE_ERR_CUDA.
+ */
+MCLAHE_API mclahe_status mclahe_forward(mclahe_plan_t plan, const float *d_in, float *d_out, void *d_ws,
+                             size_t ws_bytes, const float *d_clip, mclahe_stream_t stream);
+
+/*
+ * mclahe_backward -- adjoint of mclahe_forward (no counterpart in the paper,
+ * which does not differentiate MCLAHE).  For the scalar L with upstream
+ * gradient g = dL/d(out):
+ *   dL/dlut[k][j] = sum over voxels v and corners i with neighbour k and
+ *                   bin_k(v) = j of g_v * c_i(v)            (Eq. (12)-(13))
+ *   dL/dclip      = V * sum_k dL/dT_k, through the normalisation, the
+ *                   cumulative sum and the clip/redistribute step.
+ * The output is piecewise constant in the intensities, so dL/d(in) = 0 almost
+ * everywhere; no input gradient is produced.
+ *   d_in, d_ws    as passed to the mclahe_forward call being differentiated
+ *                 (the workspace must still hold that call's range and
+ *                 histograms).
+ *   d_grad_out    device, prod(shape) float32.
+ *   d_clip        the same clip pointer as the forward call (nullable).
+ *   d_grad_lut    nullable device float [K][n_bins]: receives dL/dlut.
+ *   d_grad_clip   device float scalar: receives dL/dclip_limit.
+ */
+MCLAHE_API mclahe_status mclahe_backward(mclahe_plan_t plan, const float *d_in, const float *d_grad_out,
+                              void *d_ws, size_t ws_bytes, const float *d_clip, float *d_grad_lut,
+                              float *d_grad_clip, mclahe_stream_t stream);
+
+/*
+ * mclahe_batch -- Algorithm 1 on n_vol independent volumes of possibly
+ * different shapes, dimensionalities and parameters (no counterpart in the
+ * paper).  Each phase runs as one persistent launch over a work list that
+ * spans all volumes.  With use_graph != 0 the launches are captured once into
+ * a CUDA graph cached in plans[0] and replayed on later calls with the same
+ * pointers.
+ *   plans     n_vol plans.
+ *   d_in      host array of n_vol device input pointers.
+ *   d_out     host array of n_vol device output pointers.
+ *   d_ws      device workspace of ws_bytes >= mclahe_batch_workspace_bytes().
+ *   d_clip    nullable device float [n_vol] clip limits.
+ */
+MCLAHE_API mclahe_status mclahe_batch(int n_vol, const mclahe_plan_t *plans, const float *const *d_in,
+                           float *const *d_out, void *d_ws, size_t ws_bytes, const float *d_clip,
+                           mclahe_stream_t stream, int use_graph);
+
+/* Workspace bytes mclahe_batch needs for these plans. */
+MCLAHE_API size_t mclahe_batch_workspace_bytes(int n_vol, const mclahe_plan_t *plans);
+
+/*
+ * mclahe_autotune -- time the candidate launch shapes of the plan's passes on
+ * the given buffers (which it overwrites) and keep the fastest in the plan.
+ * Results are cached per (D, kernel size, n_bins, range mode) for the process.
+ * Synchronises the stream.
+ */
+MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, float *d_out, void *d_ws,
+                              size_t ws_bytes, mclahe_stream_t stream);
+
+/* Synchronise `stream`, then read and clear the device status word of the
+ * workspace.  Returns MCLAHE_OK or the error device code recorded. */
+MCLAHE_API mclahe_status mclahe_sync_status(void *d_ws, mclahe_stream_t stream);
+
+/* Static description of a status code. */
+MCLAHE_API const char *mclahe_status_string(mclahe_status status);
+
+/* Library version, MAJOR * 10000 + MINOR * 100 + PATCH. */
+MCLAHE_API int mclahe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCLAHE_H */

@@ -1,0 +1,232 @@
+"""ctypes binding of libmclahe.so (the C ABI declared in include/mclahe.h).
+
+Argument marshalling only: every step of MCLAHE runs in the library's CUDA
+kernels.  The functions keep the C names; tensors may be passed wherever the C
+function takes a device pointer (their ``data_ptr()`` is used), and streams
+may be torch streams or raw handles.  There is no CPU fallback: if the library
+is missing, loading fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libmclahe.so")
+
+MCLAHE_OK = 0
+MCLAHE_ERR_INVALID_ARG = 1
+MCLAHE_ERR_UNSUPPORTED = 2
+MCLAHE_ERR_WORKSPACE = 3
+MCLAHE_ERR_CUDA = 4
+MCLAHE_ERR_TIMEOUT = 5
+MCLAHE_ERR_NO_MEMORY = 6
+MCLAHE_ERR_DEVICE = 7
+
+MCLAHE_RANGE_GLOBAL = 0
+MCLAHE_RANGE_ADAPTIVE = 1
+
+# every symbol include/mclahe.h declares
+EXPORTS = (
+    "mclahe_plan", "mclahe_plan_destroy", "mclahe_plan_query", "mclahe_workspace_bytes",
+    "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
+    "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
+)
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32), ("n_bins", ctypes.c_int32), ("mode", ctypes.c_int32),
+        ("clip_limit", ctypes.c_float),
+        ("shape", ctypes.c_int64 * 4), ("kernel_size", ctypes.c_int64 * 4),
+        ("pad", ctypes.c_int64 * 4), ("pad_before", ctypes.c_int64 * 4),
+        ("pad_after", ctypes.c_int64 * 4), ("n_kernels_dim", ctypes.c_int64 * 4),
+        ("n_kernels", ctypes.c_int64), ("kernel_voxels", ctypes.c_int64),
+        ("n_voxels", ctypes.c_int64),
+        ("ws_status", ctypes.c_size_t), ("ws_range_keys", ctypes.c_size_t),
+        ("ws_hist", ctypes.c_size_t), ("ws_lo", ctypes.c_size_t), ("ws_scale", ctypes.c_size_t),
+        ("ws_lut", ctypes.c_size_t), ("ws_scratch", ctypes.c_size_t), ("ws_bytes", ctypes.c_size_t),
+    ]
+
+    def as_dict(self):
+        d = self.ndim
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v)[:d] if isinstance(v, ctypes.Array) else v
+        return out
+
+
+class MclaheError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmclahe.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libmclahe.so not found at {path}; build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        vp, sz, i32, f32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_float
+        lib.mclahe_plan.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(i32), i32, f32, ctypes.c_int, vp]
+        lib.mclahe_plan.restype = ctypes.c_int
+        lib.mclahe_plan_destroy.argtypes = [vp]
+        lib.mclahe_plan_destroy.restype = None
+        lib.mclahe_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        lib.mclahe_plan_query.restype = ctypes.c_int
+        lib.mclahe_workspace_bytes.argtypes = [vp]
+        lib.mclahe_workspace_bytes.restype = sz
+        lib.mclahe_forward.argtypes = [vp, vp, vp, vp, sz, vp, vp]
+        lib.mclahe_forward.restype = ctypes.c_int
+        lib.mclahe_backward.argtypes = [vp, vp, vp, vp, sz, vp, vp, vp, vp]
+        lib.mclahe_backward.restype = ctypes.c_int
+        lib.mclahe_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp), vp, sz, vp, vp, ctypes.c_int]
+        lib.mclahe_batch.restype = ctypes.c_int
+        lib.mclahe_batch_workspace_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
+        lib.mclahe_batch_workspace_bytes.restype = sz
+        lib.mclahe_autotune.argtypes = [vp, vp, vp, vp, sz, vp]
+        lib.mclahe_autotune.restype = ctypes.c_int
+        lib.mclahe_sync_status.argtypes = [vp, vp]
+        lib.mclahe_sync_status.restype = ctypes.c_int
+        lib.mclahe_status_string.argtypes = [ctypes.c_int]
+        lib.mclahe_status_string.restype = ctypes.c_char_p
+        lib.mclahe_version.argtypes = []
+        lib.mclahe_version.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status, where):
+    if status != MCLAHE_OK:
+        raise MclaheError(status, where)
+
+
+def status_string(status: int) -> str:
+    return load().mclahe_status_string(int(status)).decode()
+
+
+def mclahe_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def mclahe_version() -> int:
+    return int(load().mclahe_version())
+
+
+class Plan:
+    """Owns an mclahe_plan_t; destroyed with the object."""
+
+    def __init__(self, handle, lib):
+        self.handle = handle
+        self._lib = lib
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h:
+            self._lib.mclahe_plan_destroy(h)
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def mclahe_plan(shape, kernel_size, n_bins, clip_limit, mode=MCLAHE_RANGE_GLOBAL,
+                global_range=None) -> Plan:
+    """mclahe_plan: validate parameters and build a host-side plan."""
+    lib = load()
+    d = len(shape)
+    h = ctypes.c_void_p()
+    sh = (ctypes.c_int64 * d)(*[int(v) for v in shape])
+    ks = (ctypes.c_int32 * len(kernel_size))(*[int(v) for v in kernel_size])
+    if len(kernel_size) != d:
+        raise MclaheError(MCLAHE_ERR_INVALID_ARG, "mclahe_plan")
+    rng = None if global_range is None else (ctypes.c_float * 2)(*[float(v) for v in global_range])
+    st = lib.mclahe_plan(ctypes.byref(h), d, sh, ks, int(n_bins), float(clip_limit), int(mode),
+                         ctypes.cast(rng, ctypes.c_void_p) if rng is not None else None)
+    _check(st, "mclahe_plan")
+    return Plan(h.value, lib)
+
+
+def mclahe_plan_query(plan) -> dict:
+    info = PlanInfo()
+    _check(load().mclahe_plan_query(plan.handle, ctypes.byref(info)), "mclahe_plan_query")
+    return info.as_dict()
+
+
+def mclahe_workspace_bytes(plan) -> int:
+    return int(load().mclahe_workspace_bytes(plan.handle))
+
+
+def mclahe_forward(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
+    st = load().mclahe_forward(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
+                               _ptr(d_clip), _stream(stream))
+    _check(st, "mclahe_forward")
+
+
+def mclahe_backward(plan, d_in, d_grad_out, d_ws, ws_bytes, d_clip, d_grad_lut, d_grad_clip,
+                    stream=None):
+    st = load().mclahe_backward(plan.handle, _ptr(d_in), _ptr(d_grad_out), _ptr(d_ws),
+                                int(ws_bytes), _ptr(d_clip), _ptr(d_grad_lut), _ptr(d_grad_clip),
+                                _stream(stream))
+    _check(st, "mclahe_backward")
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))(*[_ptr(x) for x in items])
+    return arr
+
+
+def mclahe_batch_workspace_bytes(plans) -> int:
+    hs = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    return int(load().mclahe_batch_workspace_bytes(len(plans), hs))
+
+
+def mclahe_batch(plans, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None, use_graph=True):
+    n = len(plans)
+    hs = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    st = load().mclahe_batch(n, hs, _ptr_array(d_in), _ptr_array(d_out), _ptr(d_ws), int(ws_bytes),
+                             _ptr(d_clip), _stream(stream), 1 if use_graph else 0)
+    _check(st, "mclahe_batch")
+
+
+def mclahe_autotune(plan, d_in, d_out, d_ws, ws_bytes, stream=None):
+    st = load().mclahe_autotune(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
+                                _stream(stream))
+    _check(st, "mclahe_autotune")
+
+
+def mclahe_sync_status(d_ws, stream=None) -> int:
+    return int(load().mclahe_sync_status(_ptr(d_ws), _stream(stream)))

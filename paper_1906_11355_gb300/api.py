@@ -1,0 +1,100 @@
+"""High-level PyTorch front end of the MCLAHE library.
+
+``MCLAHE`` holds a plan and its device workspace and runs the forward pass on
+CUDA tensors through the C ABI; ``mclahe`` is the one-call form.  PyTorch
+provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native as nat
+
+
+class MCLAHE:
+    """Plan + workspace for one volume shape (Algorithm 1 of arXiv:1906.11355).
+
+    shape, kernel_size: per-dimension extents (1..4 dims, 1 <= b <= s).
+    n_bins: histogram bins (2..4096).  clip_limit: [0, 1], T = clip_limit * V.
+    adaptive: per-kernel histogram range (Sec. III.D) instead of a global one.
+    global_range: optional (lo, hi) for the global range (else the data's).
+    """
+
+    def __init__(self, shape, kernel_size, n_bins=256, clip_limit=0.01, adaptive=False,
+                 global_range=None, device="cuda"):
+        self.shape = tuple(int(s) for s in shape)
+        self.kernel_size = tuple(int(b) for b in kernel_size)
+        self.n_bins = int(n_bins)
+        self.clip_limit = float(clip_limit)
+        self.adaptive = bool(adaptive)
+        mode = nat.MCLAHE_RANGE_ADAPTIVE if adaptive else nat.MCLAHE_RANGE_GLOBAL
+        self.plan = nat.mclahe_plan(self.shape, self.kernel_size, self.n_bins, self.clip_limit,
+                                    mode, global_range)
+        self.info = nat.mclahe_plan_query(self.plan)
+        self.device = torch.device(device)
+        self.ws_bytes = nat.mclahe_workspace_bytes(self.plan)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    @property
+    def n_kernels(self):
+        return int(self.info["n_kernels"])
+
+    def _check_volume(self, x):
+        if x.device.type != "cuda" or x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("expected a contiguous float32 CUDA tensor")
+        if tuple(x.shape) != self.shape:
+            raise ValueError(f"expected shape {self.shape}, got {tuple(x.shape)}")
+
+    def forward(self, x, out=None, clip=None, stream=None):
+        """Run Algorithm 1 on x; returns out (allocated if not given).
+
+        clip: optional 1-element float32 CUDA tensor overriding the clip limit."""
+        self._check_volume(x)
+        if out is None:
+            out = torch.empty_like(x)
+        nat.mclahe_forward(self.plan, x, out, self.ws, self.ws_bytes, clip, stream)
+        return out
+
+    __call__ = forward
+
+    def autotune(self, x, out=None, stream=None):
+        """Pick launch shapes by timing candidates on x (overwrites out)."""
+        self._check_volume(x)
+        if out is None:
+            out = torch.empty_like(x)
+        nat.mclahe_autotune(self.plan, x, out, self.ws, self.ws_bytes, stream)
+
+    # views into the workspace left by the last forward call
+    def _view(self, key, count, dtype):
+        off = int(self.info[key])
+        nbytes = count * torch.empty((), dtype=dtype).element_size()
+        return self.ws[off:off + nbytes].view(dtype)
+
+    def histograms(self):
+        """uint32 [K, n_bins] kernel histograms (as int64 for convenience)."""
+        h = self._view("ws_hist", self.n_kernels * self.n_bins, torch.int32)
+        return h.view(self.n_kernels, self.n_bins).to(torch.int64) & 0xFFFFFFFF
+
+    def tables(self):
+        """float32 [K, n_bins] mapping tables."""
+        return self._view("ws_lut", self.n_kernels * self.n_bins, torch.float32).view(
+            self.n_kernels, self.n_bins)
+
+    def ranges(self):
+        """(lo[K], scale[K]) histogram ranges of the kernels."""
+        K = self.n_kernels
+        return (self._view("ws_lo", K, torch.float32), self._view("ws_scale", K, torch.float32))
+
+
+_cache = {}
+
+
+def mclahe(x, kernel_size, n_bins=256, clip_limit=0.01, adaptive=False, global_range=None):
+    """One-call MCLAHE of a contiguous float32 CUDA tensor (plan cached)."""
+    key = (tuple(x.shape), tuple(kernel_size), int(n_bins), float(clip_limit), bool(adaptive),
+           None if global_range is None else tuple(float(v) for v in global_range), x.device)
+    op = _cache.get(key)
+    if op is None:
+        op = MCLAHE(x.shape, kernel_size, n_bins, clip_limit, adaptive, global_range, x.device)
+        _cache[key] = op
+    return op.forward(x)

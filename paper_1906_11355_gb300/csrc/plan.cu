@@ -1,0 +1,257 @@
+// plan.cu -- host side of the C ABI: plan validation and geometry
+// (Sec. III.B, Eq. (1)-(2)), workspace layout, launch-shape heuristic, the
+// forward pass orchestration (Algorithm 1) and status reporting.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include <algorithm>
+
+#include "mclahe_internal.cuh"
+
+namespace mclahe {
+
+static size_t align_up(size_t x) { return (x + kWsAlign - 1) / kWsAlign * kWsAlign; }
+
+// Number of SMs of the current device (152 on GB300), cached per process.
+int device_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            sms = v;
+        else
+            sms = 152;
+    }
+    return sms;
+}
+
+int64_t n_cells(const Geom &g) {
+    int64_t c = 1;
+    for (int j = 0; j < g.D; ++j) c *= (g.d[j].n - 1);
+    return c;
+}
+
+// Default launch shapes: enough CTAs for several waves on 152 SMs, each
+// covering at least a few thousand voxels.
+Tuning default_tuning(const Geom &g) {
+    Tuning t;
+    t.hist_threads = 256;
+    t.map_threads = 256;
+    const int64_t target = 152 * 8;
+    int64_t rows = 1;   // rows of an interior kernel footprint
+    for (int j = 0; j + 1 < g.D; ++j) rows *= g.d[j].b;
+    int64_t hc = (target + g.K - 1) / g.K;
+    hc = std::min<int64_t>(std::max<int64_t>(hc, 1), std::max<int64_t>(rows / 4, 1));
+    t.hist_chunks = int(std::min<int64_t>(hc, 64));
+    const int64_t cells = n_cells(g);
+    int64_t mc = (target + cells - 1) / cells;
+    mc = std::min<int64_t>(std::max<int64_t>(mc, 1), std::max<int64_t>(rows / 4, 1));
+    t.map_chunks = int(std::min<int64_t>(mc, 64));
+    return t;
+}
+
+Layout make_layout(const Geom &g) {
+    Layout L;
+    size_t off = 0;
+    L.status = off;
+    off = align_up(off + sizeof(uint32_t) * 4);
+    L.keys_count = (g.mode == MCLAHE_RANGE_ADAPTIVE) ? size_t(2 * g.K) : 2;
+    L.keys = off;
+    off = align_up(off + sizeof(uint32_t) * L.keys_count);
+    L.hist = off;                               // keys and hist are cleared together
+    off = align_up(off + sizeof(uint32_t) * size_t(g.K) * g.nb);
+    L.lo = off;
+    off = align_up(off + sizeof(float) * size_t(g.K));
+    L.scale = off;
+    off = align_up(off + sizeof(float) * size_t(g.K));
+    L.lut = off;
+    off = align_up(off + sizeof(float) * size_t(g.K) * g.nb);
+    // backward: per-cell partial table gradients (2^D corners x nb per cell)
+    // and per-kernel clip gradients
+    L.scratch = off;
+    L.scratch_bytes = sizeof(float) * size_t(n_cells(g)) * (size_t(1) << g.D) * g.nb +
+                      sizeof(float) * size_t(g.K);
+    off = align_up(off + L.scratch_bytes);
+    L.total = off;
+    return L;
+}
+
+mclahe_status check_forward_args(const mclahe_plan_s *p, const void *in, const void *out,
+                                 const void *ws, size_t ws_bytes) {
+    if (!p || !in || !out) return MCLAHE_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+        return MCLAHE_ERR_INVALID_ARG;
+    if (in == out) return MCLAHE_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < p->ws.total || (reinterpret_cast<uintptr_t>(ws) & (kWsAlign - 1)))
+        return MCLAHE_ERR_WORKSPACE;
+    return MCLAHE_OK;
+}
+
+mclahe_status forward_impl(const mclahe_plan_s &p, const float *in, float *out, unsigned char *ws,
+                           const float *d_clip, cudaStream_t st) {
+    const size_t clear = p.ws.hist + sizeof(uint32_t) * size_t(p.g.K) * p.g.nb - p.ws.keys;
+    if (cudaMemsetAsync(ws + p.ws.keys, 0, clear, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    if (launch_range(p, in, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    if (launch_hist(p, in, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    if (launch_lut(p, ws, d_clip, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    if (launch_map(p, in, out, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    return MCLAHE_OK;
+}
+
+}  // namespace mclahe
+
+using namespace mclahe;
+
+extern "C" {
+
+mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
+                          const int32_t *kernel_size, int32_t n_bins, float clip_limit,
+                          mclahe_range_mode mode, const float *global_range) {
+    if (!out) return MCLAHE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (ndim < 1 || ndim > kMaxDim || !shape || !kernel_size) return MCLAHE_ERR_INVALID_ARG;
+    if (n_bins < 2 || n_bins > kMaxBins) return MCLAHE_ERR_INVALID_ARG;
+    if (!(clip_limit >= 0.0f && clip_limit <= 1.0f)) return MCLAHE_ERR_INVALID_ARG;
+    if (mode != MCLAHE_RANGE_GLOBAL && mode != MCLAHE_RANGE_ADAPTIVE) return MCLAHE_ERR_INVALID_ARG;
+    if (global_range) {
+        if (mode != MCLAHE_RANGE_GLOBAL) return MCLAHE_ERR_INVALID_ARG;
+        if (!std::isfinite(global_range[0]) || !std::isfinite(global_range[1]) ||
+            global_range[1] < global_range[0])
+            return MCLAHE_ERR_INVALID_ARG;
+    }
+    Geom g;
+    std::memset(&g, 0, sizeof(g));
+    g.D = ndim;
+    g.nb = n_bins;
+    g.mode = mode;
+    g.clip = clip_limit;
+    g.has_range = global_range != nullptr;
+    g.range_lo = global_range ? global_range[0] : 0.0f;
+    g.range_hi = global_range ? global_range[1] : 0.0f;
+    g.K = 1;
+    g.V = 1;
+    g.N = 1;
+    int64_t pad[kMaxDim] = {0, 0, 0, 0};
+    for (int j = 0; j < ndim; ++j) {
+        const int64_t s = shape[j], b = kernel_size[j];
+        if (s < 1 || b < 1 || b > s) return MCLAHE_ERR_INVALID_ARG;
+        if (s > (int64_t(1) << 30)) return MCLAHE_ERR_UNSUPPORTED;
+        const int64_t p = 2 * b - 1 - ((s - 1) % b);   // Eq. (1)
+        Dim &d = g.d[j];
+        d.s = int32_t(s);
+        d.b = int32_t(b);
+        d.p0 = int32_t(p / 2);                          // Eq. (2)
+        d.p1 = int32_t((p + 1) / 2);
+        d.n = int32_t((s + p) / b);
+        pad[j] = p;
+        g.K *= d.n;
+        g.V *= b;
+        g.N *= s;
+        if (g.K > (int64_t(1) << 31) || g.V > (int64_t(1) << 31) || g.N > (int64_t(1) << 40))
+            return MCLAHE_ERR_UNSUPPORTED;
+    }
+    int64_t stride = 1;
+    for (int j = ndim - 1; j >= 0; --j) {
+        g.d[j].stride = stride;
+        stride *= g.d[j].s;
+    }
+    // mapping tables of the 2^D neighbours must fit in shared memory
+    if ((size_t(1) << ndim) * size_t(n_bins) * sizeof(float) > 200 * 1024) return MCLAHE_ERR_UNSUPPORTED;
+    // CTAs per footprint row range: counts must stay in 32 bits
+    int64_t foot = 1;
+    for (int j = 0; j < ndim; ++j) foot *= std::min<int64_t>(g.d[j].s, 2 * int64_t(g.d[j].b));
+    if (foot > (int64_t(1) << 31)) return MCLAHE_ERR_UNSUPPORTED;
+
+    mclahe_plan_s *p = new (std::nothrow) mclahe_plan_s;
+    if (!p) return MCLAHE_ERR_NO_MEMORY;
+    std::memset(p, 0, sizeof(*p));
+    p->g = g;
+    p->t = default_tuning(g);
+    p->ws = make_layout(g);
+    for (int j = 0; j < kMaxDim; ++j) p->pad[j] = pad[j];
+    p->graph_cache = nullptr;
+    *out = p;
+    return MCLAHE_OK;
+}
+
+void mclahe_plan_destroy(mclahe_plan_t plan) {
+    if (!plan) return;
+    release_graph_cache(plan);
+    delete plan;
+}
+
+mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
+    if (!p || !info) return MCLAHE_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    const Geom &g = p->g;
+    info->ndim = g.D;
+    info->n_bins = g.nb;
+    info->mode = g.mode;
+    info->clip_limit = g.clip;
+    for (int j = 0; j < g.D; ++j) {
+        info->shape[j] = g.d[j].s;
+        info->kernel_size[j] = g.d[j].b;
+        info->pad[j] = p->pad[j];
+        info->pad_before[j] = g.d[j].p0;
+        info->pad_after[j] = g.d[j].p1;
+        info->n_kernels_dim[j] = g.d[j].n;
+    }
+    info->n_kernels = g.K;
+    info->kernel_voxels = g.V;
+    info->n_voxels = g.N;
+    info->ws_status = p->ws.status;
+    info->ws_range_keys = p->ws.keys;
+    info->ws_hist = p->ws.hist;
+    info->ws_lo = p->ws.lo;
+    info->ws_scale = p->ws.scale;
+    info->ws_lut = p->ws.lut;
+    info->ws_scratch = p->ws.scratch;
+    info->ws_bytes = p->ws.total;
+    return MCLAHE_OK;
+}
+
+size_t mclahe_workspace_bytes(mclahe_plan_t p) { return p ? p->ws.total : 0; }
+
+mclahe_status mclahe_forward(mclahe_plan_t p, const float *d_in, float *d_out, void *d_ws,
+                             size_t ws_bytes, const float *d_clip, mclahe_stream_t stream) {
+    mclahe_status s = check_forward_args(p, d_in, d_out, d_ws, ws_bytes);
+    if (s != MCLAHE_OK) return s;
+    return forward_impl(*p, d_in, d_out, static_cast<unsigned char *>(d_ws), d_clip,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+mclahe_status mclahe_sync_status(void *d_ws, mclahe_stream_t stream) {
+    if (!d_ws) return MCLAHE_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, d_ws, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return MCLAHE_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    if (word != 0) {
+        if (cudaMemsetAsync(d_ws, 0, sizeof(word), st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+        return word <= MCLAHE_ERR_DEVICE ? mclahe_status(word) : MCLAHE_ERR_DEVICE;
+    }
+    return MCLAHE_OK;
+}
+
+const char *mclahe_status_string(mclahe_status s) {
+    switch (s) {
+        case MCLAHE_OK: return "ok";
+        case MCLAHE_ERR_INVALID_ARG: return "invalid argument";
+        case MCLAHE_ERR_UNSUPPORTED: return "unsupported size or parameter";
+        case MCLAHE_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+        case MCLAHE_ERR_CUDA: return "CUDA runtime error";
+        case MCLAHE_ERR_TIMEOUT: return "bounded device wait timed out";
+        case MCLAHE_ERR_NO_MEMORY: return "host allocation failed";
+        case MCLAHE_ERR_DEVICE: return "device code reported an error";
+    }
+    return "unknown status";
+}
+
+int mclahe_version(void) { return 100; }
+
+}  // extern "C"

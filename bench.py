@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Throughput of the MCLAHE hot path on GB300 (one JSON line on stdout).
+
+A step is one full forward pass (range, histograms, tables, mapping) over one
+synthetic volume already resident in HBM.  The default workload is the 3-D
+fluorescence-like stack 64x512x512 (kernel 16x64x64, 256 bins, clip 0.02,
+adaptive range).  L2 is flushed (a 256 MiB write) between timed steps, outside
+the step's events.  Each pass is timed with CUDA events on the stream that
+launches it; the step time is the first-to-last event span.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU oracle on this host
+
+Under torchrun (N > 1) each rank processes its own volume (different seed) with
+no data exchange (weak scaling); rank 0 prints the whole-job throughput from
+the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MCLAHE Gvoxel/s & % HBM roofline; batched and fwd+bwd vs plain fwd"
+DEFAULT_WORKLOAD = "3d-fluorescence-64x512x512"
+L2_FLUSH_BYTES = 256 << 20
+PEAK_FALLBACK_GBS = 6800.0
+
+# kernel launched by each pass (for the roofline and the ncu launch list)
+PASS_KERNEL = {"range": "k_range", "hist": "k_hist", "lut": "k_lut", "map": "k_map"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region (nvidia-smi sampled in the background)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        def parse(line):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                return None
+            try:
+                return dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                            hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8])
+            except ValueError:
+                return None
+
+        inside = [parse(l) for t, l in self.samples if t0 <= t <= t1]
+        inside = [s for s in inside if s]
+        window = "timed"
+        if not inside:   # region shorter than the sampling period
+            inside = [s for s in (parse(l) for _, l in self.samples) if s]
+            window = "warmup+timed"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sms = sorted(s["sm"] for s in inside)
+        reasons = set()
+        for s in inside:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if s[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(s["smax"] for s in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+                "power_w_max": max(s["power"] for s in inside)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch of each pass (HBM roofline)
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(info, adaptive, has_range):
+    N = info["n_voxels"]
+    K = info["n_kernels"]
+    nb = info["n_bins"]
+    D = info["ndim"]
+    b = {
+        "range": 0 if (not adaptive and has_range) else 4 * N,
+        "hist": 4 * N + 4 * K * nb,
+        "lut": 4 * K * nb + 4 * K * nb + 8 * K,
+        "map": 8 * N,
+    }
+    return b
+
+
+def kernel_source_hash(pass_name):
+    fn = {"range": "k_range.cu", "hist": "k_hist.cu", "lut": "k_lut.cu", "map": "k_map.cu"}[pass_name]
+    h = hashlib.sha256()
+    for f in (fn, "mclahe_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1906_11355_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, pass_name):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[workload][pass_name]
+    except Exception:
+        return None
+    if rec.get("source_sha") != kernel_source_hash(pass_name):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on this host's cores
+# ---------------------------------------------------------------------------
+def oracle_rate(x, w, min_seconds=10.0):
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    clip = float(np.float32(w["clip_limit"]))
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.mclahe(x, w["kernel"], w["n_bins"], clip, mode=int(w["adaptive"]))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return x.size * reps / el / 1e9, reps, el, cores
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1906_11355_gb300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    x = synth.make_volume(w["gen"], w["shape"], w["seed"])
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    clip = float(np.float32(w["clip_limit"]))
+    # bound the whole run to about two minutes: shrink the volume along dim 0
+    # (whole kernels) when K full-volume steps would take longer
+    t0 = time.perf_counter()
+    oracle.mclahe(x, w["kernel"], w["n_bins"], clip, mode=int(w["adaptive"]))
+    t_full = time.perf_counter() - t0
+    sample = f"the whole {args.workload} volume per step"
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    if t_full > budget:
+        b0 = w["kernel"][0]
+        s0 = max(b0, int(w["shape"][0] * budget / t_full) // b0 * b0)
+        x = np.ascontiguousarray(x[:s0])
+        sample = f"leading {s0} of {w['shape'][0]} slices of the {args.workload} volume per step"
+    for _ in range(max(args.warmup, 0)):
+        oracle.mclahe(x, w["kernel"], w["n_bins"], clip, mode=int(w["adaptive"]))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mclahe(x, w["kernel"], w["n_bins"], clip, mode=int(w["adaptive"]))
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = x.size / (ms * 1e-3) / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gvoxel/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "shape": list(w["shape"]), "kernel": list(w["kernel"]),
+                   "n_bins": w["n_bins"], "clip_limit": w["clip_limit"],
+                   "range": "adaptive" if w["adaptive"] else "global"},
+        "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300 import build as nbuild
+    from paper_1906_11355_gb300 import synth
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    nbuild.build()
+    nat.load()
+    w = synth.WORKLOADS[args.workload]
+    x_host = synth.make_volume(w["gen"], w["shape"], w["seed"] + 7919 * rank)
+    op = MCLAHE(w["shape"], w["kernel"], w["n_bins"], float(np.float32(w["clip_limit"])),
+                adaptive=w["adaptive"], device=dev)
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    passes = list(range(nat.MCLAHE_N_PASSES))
+    launches = {p: nat.mclahe_pass_launches(op.plan, p) for p in passes}
+
+    def step(evs):
+        evs[0].record(stream)
+        for p in passes:
+            nat.mclahe_forward_pass(op.plan, p, x, out, op.ws, op.ws_bytes, None, stream)
+            evs[p + 1].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step([torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)])
+    torch.cuda.synchronize(dev)
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)]
+              for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.time()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                 # evict the previous step's lines from L2
+        step(events[i])
+    torch.cuda.synchronize(dev)
+    t1 = time.time()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+
+    step_ms = [ev[0].elapsed_time(ev[-1]) for ev in events]
+    pass_ms = {nat.PASS_NAMES[p]: sum(ev[p].elapsed_time(ev[p + 1]) for ev in events) / args.steps
+               for p in passes}
+    ms = sum(step_ms) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    voxels = int(np.prod(w["shape"]))
+    value = voxels * world / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host -> device, forward, device -> host
+    e2e = None
+    if rank == 0 or world > 1:
+        h_in = torch.from_numpy(x_host).pin_memory()
+        h_out = torch.empty(h_in.shape, dtype=torch.float32).pin_memory()
+        for _ in range(3):
+            op.forward(h_in.to(dev, non_blocking=True), out=out)
+            h_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            xd = h_in.to(dev, non_blocking=True)
+            op.forward(xd, out=out)
+            h_out.copy_(out, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+        e2e = {"value": voxels * world / (e2e_ms * 1e-3) / 1e9, "unit": "Gvoxel/s",
+               "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4),
+               "ms_per_step": e2e_ms}
+
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peak_gbs()
+    algo = algorithmic_bytes(op.info, w["adaptive"], False)
+    kern = {k: v for k, v in pass_ms.items() if k in PASS_KERNEL and launches[nat.PASS_NAMES.index(k)] > 0}
+    dom = max(kern, key=kern.get)
+    achieved = algo[dom] / (pass_ms[dom] * 1e-3) / 1e9
+    traffic = recorded_traffic(args.workload, dom)
+    roofline = {"bound": "hbm", "kernel": PASS_KERNEL[dom], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": peak_kind, "algorithmic_bytes": algo[dom]}
+    whole = 12 * voxels / (ms * 1e-3) / 1e9    # 2 input reads + 1 output write
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, reps, el, cores = oracle_rate(x_host, w)
+        cpu = {"value": rate, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
+               "sample": f"whole {args.workload} volume x{reps} ({el:.1f} s, FP64, OpenMP)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "shape": list(w["shape"]), "kernel": list(w["kernel"]),
+                   "n_bins": w["n_bins"], "clip_limit": w["clip_limit"],
+                   "range": "adaptive" if w["adaptive"] else "global",
+                   "l2": "flushed between steps (256 MiB write outside the step events)",
+                   "voxels_per_gpu": voxels},
+        "hbm_roofline_frac_whole_step": whole / peak,
+        "passes_ms": pass_ms,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(sum(launches.values()) * args.steps),
+        "clocks": sampler.summary(t0, t1),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

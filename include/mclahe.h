@@ -156,6 +156,31 @@ MCLAHE_API size_t mclahe_workspace_bytes(mclahe_plan_t plan);
 MCLAHE_API mclahe_status mclahe_forward(mclahe_plan_t plan, const float *d_in, float *d_out, void *d_ws,
                              size_t ws_bytes, const float *d_clip, mclahe_stream_t stream);
 
+/* The passes of mclahe_forward, in the order it runs them. */
+typedef enum {
+    MCLAHE_PASS_CLEAR = 0,  /* zero the range keys and histograms (memset) */
+    MCLAHE_PASS_RANGE = 1,  /* histogram ranges, Sec. III.D (no launch for a given GHR range) */
+    MCLAHE_PASS_HIST = 2,   /* per-kernel histograms, Algorithm 1 */
+    MCLAHE_PASS_LUT = 3,    /* clip, redistribute, CDF, normalise, Algorithm 1 */
+    MCLAHE_PASS_MAP = 4,    /* multilinear mapping, Sec. III.C, Eq. (12)-(13) */
+    MCLAHE_N_PASSES = 5
+} mclahe_pass;
+
+/*
+ * mclahe_forward_pass -- run one pass of mclahe_forward (same arguments and
+ * errors).  Calling passes CLEAR..MAP in order on one stream is exactly
+ * mclahe_forward; single passes let a caller time or reuse them (for example
+ * re-run MAP with tables it has left in the workspace).  d_out may be NULL for
+ * every pass but MAP.
+ */
+MCLAHE_API mclahe_status mclahe_forward_pass(mclahe_plan_t plan, mclahe_pass pass, const float *d_in,
+                                             float *d_out, void *d_ws, size_t ws_bytes,
+                                             const float *d_clip, mclahe_stream_t stream);
+
+/* Number of this library's kernels a pass launches for this plan (0 for
+ * CLEAR, which is a memset, and for RANGE with a caller-given global range). */
+MCLAHE_API int mclahe_pass_launches(mclahe_plan_t plan, mclahe_pass pass);
+
 /*
  * mclahe_backward -- adjoint of mclahe_forward (no counterpart in the paper,
  * which does not differentiate MCLAHE).  For the scalar L with upstream

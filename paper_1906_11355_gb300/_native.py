@@ -32,7 +32,12 @@ EXPORTS = (
     "mclahe_plan", "mclahe_plan_destroy", "mclahe_plan_query", "mclahe_workspace_bytes",
     "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
+    "mclahe_forward_pass", "mclahe_pass_launches",
 )
+
+MCLAHE_PASS_CLEAR, MCLAHE_PASS_RANGE, MCLAHE_PASS_HIST, MCLAHE_PASS_LUT, MCLAHE_PASS_MAP = range(5)
+MCLAHE_N_PASSES = 5
+PASS_NAMES = ("clear", "range", "hist", "lut", "map")
 
 
 class PlanInfo(ctypes.Structure):
@@ -104,6 +109,10 @@ def load(path: str = LIB_PATH):
         lib.mclahe_sync_status.restype = ctypes.c_int
         lib.mclahe_status_string.argtypes = [ctypes.c_int]
         lib.mclahe_status_string.restype = ctypes.c_char_p
+        lib.mclahe_forward_pass.argtypes = [vp, ctypes.c_int, vp, vp, vp, sz, vp, vp]
+        lib.mclahe_forward_pass.restype = ctypes.c_int
+        lib.mclahe_pass_launches.argtypes = [vp, ctypes.c_int]
+        lib.mclahe_pass_launches.restype = ctypes.c_int
         lib.mclahe_version.argtypes = []
         lib.mclahe_version.restype = ctypes.c_int
         _lib = lib
@@ -194,6 +203,16 @@ def mclahe_forward(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
     st = load().mclahe_forward(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
                                _ptr(d_clip), _stream(stream))
     _check(st, "mclahe_forward")
+
+
+def mclahe_forward_pass(plan, pass_, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
+    st = load().mclahe_forward_pass(plan.handle, int(pass_), _ptr(d_in), _ptr(d_out), _ptr(d_ws),
+                                    int(ws_bytes), _ptr(d_clip), _stream(stream))
+    _check(st, "mclahe_forward_pass")
+
+
+def mclahe_pass_launches(plan, pass_) -> int:
+    return int(load().mclahe_pass_launches(plan.handle, int(pass_)))
 
 
 def mclahe_backward(plan, d_in, d_grad_out, d_ws, ws_bytes, d_clip, d_grad_lut, d_grad_clip,

@@ -90,14 +90,30 @@ mclahe_status check_forward_args(const mclahe_plan_s *p, const void *in, const v
     return MCLAHE_OK;
 }
 
+mclahe_status run_pass(const mclahe_plan_s &p, int pass, const float *in, float *out,
+                       unsigned char *ws, const float *d_clip, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    switch (pass) {
+        case MCLAHE_PASS_CLEAR: {
+            const size_t clear = p.ws.hist + sizeof(uint32_t) * size_t(p.g.K) * p.g.nb - p.ws.keys;
+            e = cudaMemsetAsync(ws + p.ws.keys, 0, clear, st);
+            break;
+        }
+        case MCLAHE_PASS_RANGE: e = launch_range(p, in, ws, st); break;
+        case MCLAHE_PASS_HIST: e = launch_hist(p, in, ws, st); break;
+        case MCLAHE_PASS_LUT: e = launch_lut(p, ws, d_clip, st); break;
+        case MCLAHE_PASS_MAP: e = launch_map(p, in, out, ws, st); break;
+        default: return MCLAHE_ERR_INVALID_ARG;
+    }
+    return e == cudaSuccess ? MCLAHE_OK : MCLAHE_ERR_CUDA;
+}
+
 mclahe_status forward_impl(const mclahe_plan_s &p, const float *in, float *out, unsigned char *ws,
                            const float *d_clip, cudaStream_t st) {
-    const size_t clear = p.ws.hist + sizeof(uint32_t) * size_t(p.g.K) * p.g.nb - p.ws.keys;
-    if (cudaMemsetAsync(ws + p.ws.keys, 0, clear, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
-    if (launch_range(p, in, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
-    if (launch_hist(p, in, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
-    if (launch_lut(p, ws, d_clip, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
-    if (launch_map(p, in, out, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    for (int pass = MCLAHE_PASS_CLEAR; pass < MCLAHE_N_PASSES; ++pass) {
+        mclahe_status s = run_pass(p, pass, in, out, ws, d_clip, st);
+        if (s != MCLAHE_OK) return s;
+    }
     return MCLAHE_OK;
 }
 
@@ -221,6 +237,36 @@ mclahe_status mclahe_forward(mclahe_plan_t p, const float *d_in, float *d_out, v
     if (s != MCLAHE_OK) return s;
     return forward_impl(*p, d_in, d_out, static_cast<unsigned char *>(d_ws), d_clip,
                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+mclahe_status mclahe_forward_pass(mclahe_plan_t p, mclahe_pass pass, const float *d_in,
+                                  float *d_out, void *d_ws, size_t ws_bytes, const float *d_clip,
+                                  mclahe_stream_t stream) {
+    if (pass < MCLAHE_PASS_CLEAR || pass >= MCLAHE_N_PASSES) return MCLAHE_ERR_INVALID_ARG;
+    mclahe_status s;
+    if (pass == MCLAHE_PASS_MAP) {
+        s = check_forward_args(p, d_in, d_out, d_ws, ws_bytes);
+    } else {
+        // a 16-aligned dummy stands in for the unused output
+        s = check_forward_args(p, d_in, reinterpret_cast<const void *>(uintptr_t(16)), d_ws, ws_bytes);
+        if (s == MCLAHE_OK && d_out && (reinterpret_cast<uintptr_t>(d_out) & 15))
+            s = MCLAHE_ERR_INVALID_ARG;
+    }
+    if (s != MCLAHE_OK) return s;
+    return run_pass(*p, pass, d_in, d_out, static_cast<unsigned char *>(d_ws), d_clip,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+int mclahe_pass_launches(mclahe_plan_t p, mclahe_pass pass) {
+    if (!p) return 0;
+    switch (pass) {
+        case MCLAHE_PASS_RANGE:
+            return (p->g.mode == MCLAHE_RANGE_GLOBAL && p->g.has_range) ? 0 : 1;
+        case MCLAHE_PASS_HIST:
+        case MCLAHE_PASS_LUT:
+        case MCLAHE_PASS_MAP: return 1;
+        default: return 0;
+    }
 }
 
 mclahe_status mclahe_sync_status(void *d_ws, mclahe_stream_t stream) {

@@ -232,6 +232,33 @@ MCLAHE_API size_t mclahe_batch_workspace_bytes(int n_vol, const mclahe_plan_t *p
 MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, float *d_out, void *d_ws,
                               size_t ws_bytes, mclahe_stream_t stream);
 
+/* Size of the library's built-in scratch array used by mclahe_forward_noalloc. */
+#define MCLAHE_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * mclahe_forward_noalloc -- mclahe_forward for callers that cannot allocate
+ * device memory.  The paper has no counterpart; it exists because some callers
+ * cannot provide the workspace mclahe_forward needs: plugin or custom-operator
+ * interfaces that pass only input and output buffers, code running where an
+ * allocation is forbidden or would break a fixed memory budget, and foreign
+ * callers without a CUDA allocator.
+ *   d_in, d_out, d_clip, stream   as for mclahe_forward.
+ * The workspace comes from one array of MCLAHE_NOALLOC_SCRATCH_BYTES built into
+ * the library, which every GPU that uses the library keeps until the process
+ * exits.  This call allocates nothing.  The first call on each device looks up
+ * the array's device address (with that device current) and caches it; make
+ * that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (the parts that must start at zero are cleared
+ * by every call), so calls that overlap on the GPU race with each other; run
+ * them on one stream or otherwise one after another.
+ * Returns MCLAHE_ERR_UNSUPPORTED when the plan's forward workspace (the offset
+ * ws_scratch of mclahe_plan_info) exceeds MCLAHE_NOALLOC_SCRATCH_BYTES,
+ * MCLAHE_ERR_INVALID_ARG for NULL, aliased or misaligned pointers, and
+ * MCLAHE_ERR_CUDA if the address lookup or a launch fails.
+ */
+MCLAHE_API mclahe_status mclahe_forward_noalloc(mclahe_plan_t plan, const float *d_in, float *d_out,
+                                                const float *d_clip, mclahe_stream_t stream);
+
 /* Synchronise `stream`, then read and clear the device status word of the
  * workspace.  Returns MCLAHE_OK or the error device code recorded. */
 MCLAHE_API mclahe_status mclahe_sync_status(void *d_ws, mclahe_stream_t stream);

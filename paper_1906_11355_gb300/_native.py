@@ -32,8 +32,10 @@ EXPORTS = (
     "mclahe_plan", "mclahe_plan_destroy", "mclahe_plan_query", "mclahe_workspace_bytes",
     "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
-    "mclahe_forward_pass", "mclahe_pass_launches",
+    "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
 )
+
+MCLAHE_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 MCLAHE_PASS_CLEAR, MCLAHE_PASS_RANGE, MCLAHE_PASS_HIST, MCLAHE_PASS_LUT, MCLAHE_PASS_MAP = range(5)
 MCLAHE_N_PASSES = 5
@@ -113,6 +115,8 @@ def load(path: str = LIB_PATH):
         lib.mclahe_forward_pass.restype = ctypes.c_int
         lib.mclahe_pass_launches.argtypes = [vp, ctypes.c_int]
         lib.mclahe_pass_launches.restype = ctypes.c_int
+        lib.mclahe_forward_noalloc.argtypes = [vp, vp, vp, vp, vp]
+        lib.mclahe_forward_noalloc.restype = ctypes.c_int
         lib.mclahe_version.argtypes = []
         lib.mclahe_version.restype = ctypes.c_int
         _lib = lib
@@ -203,6 +207,13 @@ def mclahe_forward(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
     st = load().mclahe_forward(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
                                _ptr(d_clip), _stream(stream))
     _check(st, "mclahe_forward")
+
+
+def mclahe_forward_noalloc(plan, d_in, d_out, d_clip=None, stream=None):
+    """Forward pass using the library's built-in scratch array (allocates nothing)."""
+    st = load().mclahe_forward_noalloc(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_clip),
+                                       _stream(stream))
+    _check(st, "mclahe_forward_noalloc")
 
 
 def mclahe_forward_pass(plan, pass_, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):

@@ -36,7 +36,7 @@ L2_FLUSH_BYTES = 256 << 20
 PEAK_FALLBACK_GBS = 6800.0
 
 # kernel launched by each pass (for the roofline and the ncu launch list)
-PASS_KERNEL = {"range": "k_range", "hist": "k_hist", "lut": "k_lut", "map": "k_map"}
+PASS_KERNEL = {"range": "k_range_global", "hist": "k_hist", "map": "k_map"}
 
 
 def parse():
@@ -145,17 +145,20 @@ def algorithmic_bytes(info, adaptive, has_range):
     K = info["n_kernels"]
     nb = info["n_bins"]
     D = info["ndim"]
+    # range: one read of the input (global range only; the adaptive ranges are
+    # found inside the histogram pass, which reads each voxel once from HBM);
+    # hist: input read + histogram and table writes; map: input read + output write
     b = {
-        "range": 0 if (not adaptive and has_range) else 4 * N,
-        "hist": 4 * N + 4 * K * nb,
-        "lut": 4 * K * nb + 4 * K * nb + 8 * K,
+        "range": 0 if (adaptive or has_range) else 4 * N,
+        "hist": 4 * N + 8 * K * nb + 8 * K,
+        "lut": 0,
         "map": 8 * N,
     }
     return b
 
 
 def kernel_source_hash(pass_name):
-    fn = {"range": "k_range.cu", "hist": "k_hist.cu", "lut": "k_lut.cu", "map": "k_map.cu"}[pass_name]
+    fn = {"range": "k_range.cu", "hist": "k_hist.cu", "map": "k_map.cu"}[pass_name]
     h = hashlib.sha256()
     for f in (fn, "mclahe_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1906_11355_gb300", "csrc", f), "rb") as fh:

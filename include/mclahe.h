@@ -158,10 +158,11 @@ MCLAHE_API mclahe_status mclahe_forward(mclahe_plan_t plan, const float *d_in, f
 
 /* The passes of mclahe_forward, in the order it runs them. */
 typedef enum {
-    MCLAHE_PASS_CLEAR = 0,  /* zero the range keys and histograms (memset) */
-    MCLAHE_PASS_RANGE = 1,  /* histogram ranges, Sec. III.D (no launch for a given GHR range) */
-    MCLAHE_PASS_HIST = 2,   /* per-kernel histograms, Algorithm 1 */
-    MCLAHE_PASS_LUT = 3,    /* clip, redistribute, CDF, normalise, Algorithm 1 */
+    MCLAHE_PASS_CLEAR = 0,  /* zero the global range keys (memset; nothing else needs it) */
+    MCLAHE_PASS_RANGE = 1,  /* global range, Sec. III.D (launches only for GHR without a range) */
+    MCLAHE_PASS_HIST = 2,   /* adaptive ranges, per-kernel histograms, clip, redistribute,
+                               CDF and normalisation (Algorithm 1), one cluster per kernel */
+    MCLAHE_PASS_LUT = 3,    /* no work: the tables are built by MCLAHE_PASS_HIST */
     MCLAHE_PASS_MAP = 4,    /* multilinear mapping, Sec. III.C, Eq. (12)-(13) */
     MCLAHE_N_PASSES = 5
 } mclahe_pass;

@@ -1,8 +1,7 @@
 // k_range.cu -- histogram ranges (Sec. III.D).
 //   GHR: min and max of the whole input (the mirror padding of Sec. III.B
 //        repeats voxels, so it changes neither).
-//   AHR: min and max of every kernel of the padded volume, read through the
-//        kernel's footprint in the original volume.
+//   (The per-kernel ranges of AHR are computed inside the histogram pass.)
 // Results are order-preserving uint32 keys combined with atomicMax; the min
 // is stored complemented so that every key starts at 0 (one memset).
 #include <algorithm>
@@ -71,58 +70,6 @@ __global__ void __launch_bounds__(256) k_range_global(const float *__restrict__ 
     }
 }
 
-// AHR: one CTA per (kernel, chunk of footprint rows).
-template <int D>
-__global__ void __launch_bounds__(256) k_range_kernels(Geom g, const float *__restrict__ in,
-                                                       uint32_t *__restrict__ keys, int chunks) {
-    const int64_t k = blockIdx.x / chunks;
-    const int chunk = blockIdx.x - int(k * chunks);
-    int kk[kMaxDim];
-    {
-        int64_t r = k;
-#pragma unroll
-        for (int j = D - 1; j >= 0; --j) {
-            kk[j] = int(r % g.d[j].n);
-            r /= g.d[j].n;
-        }
-    }
-    int lo[kMaxDim], len[kMaxDim];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        Foot f = footprint(g.d[j], kk[j]);
-        lo[j] = f.lo;
-        len[j] = f.hi - f.lo;
-    }
-    int R = 1;
-#pragma unroll
-    for (int j = 0; j < D - 1; ++j) R *= len[j];
-    const int r0 = int((int64_t(R) * chunk) / chunks);
-    const int r1 = int((int64_t(R) * (chunk + 1)) / chunks);
-    const int L = len[D - 1];
-
-    float mn = INFINITY, mx = -INFINITY;
-    // lanes of a warp walk one row, warps take rows in turn
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    RowIter<D> it;
-    it.init(len, r0 + warp, nw);
-    for (int r = r0 + warp; r < r1; r += nw) {
-        int64_t base = lo[D - 1];
-#pragma unroll
-        for (int j = 0; j < D - 1; ++j) base += int64_t(lo[j] + it.c[j]) * g.d[j].stride;
-        for (int x = lane; x < L; x += 32) {
-            float v = in[base + x];
-            mn = fminf(mn, v);
-            mx = fmaxf(mx, v);
-        }
-        it.next();
-    }
-    block_minmax(mn, mx);
-    if (threadIdx.x == 0 && r1 > r0) {
-        atomicMax(&keys[2 * k], ~float_key(mn));
-        atomicMax(&keys[2 * k + 1], float_key(mx));
-    }
-}
-
 cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                          cudaStream_t st) {
     const Geom &g = p.g;
@@ -134,16 +81,7 @@ cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char 
         k_range_global<<<blocks, 256, 0, st>>>(in, g.N, keys);
         return cudaGetLastError();
     }
-    const int chunks = p.t.hist_chunks;
-    const unsigned grid = unsigned(g.K * chunks);
-    switch (g.D) {
-        case 1: k_range_kernels<1><<<grid, 256, 0, st>>>(g, in, keys, chunks); break;
-        case 2: k_range_kernels<2><<<grid, 256, 0, st>>>(g, in, keys, chunks); break;
-        case 3: k_range_kernels<3><<<grid, 256, 0, st>>>(g, in, keys, chunks); break;
-        case 4: k_range_kernels<4><<<grid, 256, 0, st>>>(g, in, keys, chunks); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return cudaSuccess;   // the adaptive range is fused into the histogram pass
 }
 
 }  // namespace mclahe

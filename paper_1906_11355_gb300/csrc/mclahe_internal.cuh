@@ -121,6 +121,18 @@ __device__ __forceinline__ int quantise(float x, float lo, float scale, float to
     return __float2int_rd(y);
 }
 
+// The same quantiser returning the bits of the float 2^23 + bin: after the
+// clamp, y lies in [0, nb - 1], where adding 2^23 rounded down is exactly
+// 2^23 + floor(y) (the float spacing there is 1).  Callers fold the constant
+// 0x4B000000 into their address arithmetic, which avoids the quarter-rate
+// float-to-int conversion.
+constexpr uint32_t kBinBias = 0x4B000000u;   // bits of 2^23
+__device__ __forceinline__ uint32_t quantise_bits(float x, float lo, float scale, float top) {
+    float y = __fmul_rn(__fsub_rn(x, lo), scale);
+    y = fminf(fmaxf(y, 0.0f), top);
+    return __float_as_uint(__fadd_rd(y, 8388608.0f));
+}
+
 // Footprint of kernel k along one dimension: the original indices whose
 // mirror images (Sec. III.B) fall in the padded interval [k*b, k*b + b).
 // Multiplicity = number of images of x in that interval (0..3).
@@ -206,14 +218,139 @@ struct RowIter {
 };
 
 // ---------------------------------------------------------------------------
+// Row walker: the CTA visits rows [r0, r1) of a box (rows = all dims but the
+// last, each row L contiguous elements from element xl of the last dim) in
+// aligned 128-bit quads.  Every thread takes four quads per step, issuing the
+// four loads before using them:
+//   RU = 1: four quads of one row (lpr lanes share a row),
+//   RU = 2: two quads from each of two rows (rows of at most 2 quads),
+//   RU = 4: one quad from each of four rows (rows of 1 quad).
+// The step count is the same for all threads of the block, so warp-wide
+// primitives may be used inside.
+// ---------------------------------------------------------------------------
+struct WalkShape {
+    int Q;      // quads per row (upper bound, including the alignment head)
+    int ru;     // rows per thread step (1, 2 or 4)
+    int lpr;    // lanes per row (RU = 1), else 1
+    int ql;     // quads per lane per row (RU = 1)
+    int G;      // row groups of the block (blockDim / lpr)
+};
+
+__device__ __forceinline__ WalkShape walk_shape(int L, int xl, bool same_align, int nthreads) {
+    WalkShape w;
+    w.Q = (((same_align ? (xl & 3) : 3) + L + 3) >> 2);
+    if (w.Q <= 1) {
+        w.ru = 4;
+        w.lpr = 1;
+        w.ql = 1;
+    } else if (w.Q == 2) {
+        w.ru = 2;
+        w.lpr = 1;
+        w.ql = 2;
+    } else {
+        w.ru = 1;
+        const int want = (w.Q + 3) >> 2;
+        int lpr = 1;
+        while (lpr < want && lpr < 32) lpr <<= 1;
+        w.lpr = lpr;
+        w.ql = (w.Q + lpr - 1) / lpr;
+    }
+    w.G = nthreads / w.lpr;
+    return w;
+}
+
+// One quad handed to the consumer: its four values, the element offset of its
+// first element inside the row (may be negative for the alignment head), and
+// its element address.
+struct QuadRef {
+    float4 v;
+    int e0;
+    int64_t a;
+    bool has;   // overlaps the row
+};
+
+__device__ __forceinline__ float4 load_quad4(const float *__restrict__ in, int64_t a, int64_t N,
+                                             bool has, bool stream) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (has) {
+        if (a + 4 <= N) {
+            v = stream ? __ldcs(reinterpret_cast<const float4 *>(in + a))
+                       : __ldg(reinterpret_cast<const float4 *>(in + a));
+        } else {
+            v.x = in[a];
+            if (a + 1 < N) v.y = in[a + 1];
+            if (a + 2 < N) v.z = in[a + 2];
+        }
+    }
+    return v;
+}
+
+// Walks the rows of a box.  row_fn(const int *coords, int64_t row_start, S &state)
+// prepares per-row state S; quad_fn(S &state, const QuadRef &q) consumes one
+// quad.  Template parameter RU must equal shape.ru.
+template <int D, int RU, typename S, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_rows(const float *__restrict__ in, int64_t N,
+                                          const int64_t *stride, const int *box_lo,
+                                          const int *box_len, int r0, int r1,
+                                          const WalkShape &w, bool stream, RowFn row_fn,
+                                          QuadFn quad_fn) {
+    const int L = box_len[D - 1];
+    const int xl = box_lo[D - 1];
+    const int grp = threadIdx.x / w.lpr, gl = threadIdx.x & (w.lpr - 1);
+    const int rows = r1 - r0;
+    const int row_steps = (rows + w.G * RU - 1) / (w.G * RU);
+    RowIter<D> it;
+    it.init(box_len, r0 + grp, w.G);
+    for (int rs = 0; rs < row_steps; ++rs) {
+        S st[RU];
+        int64_t start[RU];
+        bool row_ok[RU];
+#pragma unroll
+        for (int ru = 0; ru < RU; ++ru) {
+            const int r = grp + (rs * RU + ru) * w.G;
+            row_ok[ru] = r < rows;
+            int64_t s = xl;
+            int coords[kMaxDim];
+#pragma unroll
+            for (int j = 0; j < D - 1; ++j) {
+                coords[j] = box_lo[j] + it.c[j];
+                s += int64_t(coords[j]) * stride[j];
+            }
+            start[ru] = s;
+            row_fn(coords, s, st[ru]);
+            it.next();
+        }
+        const int qsteps = (RU == 1) ? (w.ql + 3) >> 2 : 1;
+        for (int qs = 0; qs < qsteps; ++qs) {
+            QuadRef q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ru = (RU == 1) ? 0 : (RU == 2 ? (u >> 1) : u);
+                const int qi = (RU == 1) ? (gl + (qs * 4 + u) * w.lpr) : (RU == 2 ? (u & 1) : 0);
+                const int64_t qbase = start[ru] & ~int64_t(3);
+                const int head = int(start[ru] - qbase);
+                q[u].e0 = 4 * qi - head;
+                q[u].a = qbase + 4 * int64_t(qi);
+                const bool inl = (RU == 1) ? ((qs * 4 + u) < w.ql) : true;
+                q[u].has = row_ok[ru] && inl && q[u].e0 < L && q[u].e0 + 4 > 0;
+                q[u].v = load_quad4(in, q[u].a, N, q[u].has, stream);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ru = (RU == 1) ? 0 : (RU == 2 ? (u >> 1) : u);
+                quad_fn(st[ru], q[u]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------
 cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                          cudaStream_t st);
 cudaError_t launch_hist(const mclahe_plan_s &p, const float *in, unsigned char *ws,
-                        cudaStream_t st);
-cudaError_t launch_lut(const mclahe_plan_s &p, unsigned char *ws, const float *d_clip,
-                       cudaStream_t st);
+                        const float *d_clip, cudaStream_t st);
 cudaError_t launch_map(const mclahe_plan_s &p, const float *in, float *out,
                        const unsigned char *ws, cudaStream_t st);
 

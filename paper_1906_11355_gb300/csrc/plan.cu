@@ -43,9 +43,12 @@ Tuning default_tuning(const Geom &g) {
     const int64_t target = 152 * 8;
     int64_t rows = 1;   // rows of an interior kernel footprint
     for (int j = 0; j + 1 < g.D; ++j) rows *= g.d[j].b;
+    // the CTAs of one kernel form a cluster (at most 8, the portable size)
     int64_t hc = (target + g.K - 1) / g.K;
     hc = std::min<int64_t>(std::max<int64_t>(hc, 1), std::max<int64_t>(rows / 4, 1));
-    t.hist_chunks = int(std::min<int64_t>(hc, 64));
+    int c = 1;
+    while (c < hc && c < 8) c <<= 1;
+    t.hist_chunks = c;
     const int64_t cells = n_cells(g);
     int64_t mc = (target + cells - 1) / cells;
     mc = std::min<int64_t>(std::max<int64_t>(mc, 1), std::max<int64_t>(rows / 4, 1));
@@ -94,14 +97,14 @@ mclahe_status run_pass(const mclahe_plan_s &p, int pass, const float *in, float 
                        unsigned char *ws, const float *d_clip, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     switch (pass) {
-        case MCLAHE_PASS_CLEAR: {
-            const size_t clear = p.ws.hist + sizeof(uint32_t) * size_t(p.g.K) * p.g.nb - p.ws.keys;
-            e = cudaMemsetAsync(ws + p.ws.keys, 0, clear, st);
+        case MCLAHE_PASS_CLEAR:
+            // only the global range keys are accumulated with atomics
+            if (p.g.mode == MCLAHE_RANGE_GLOBAL && !p.g.has_range)
+                e = cudaMemsetAsync(ws + p.ws.keys, 0, 2 * sizeof(uint32_t), st);
             break;
-        }
         case MCLAHE_PASS_RANGE: e = launch_range(p, in, ws, st); break;
-        case MCLAHE_PASS_HIST: e = launch_hist(p, in, ws, st); break;
-        case MCLAHE_PASS_LUT: e = launch_lut(p, ws, d_clip, st); break;
+        case MCLAHE_PASS_HIST: e = launch_hist(p, in, ws, d_clip, st); break;
+        case MCLAHE_PASS_LUT: break;   // built by the histogram pass's clusters
         case MCLAHE_PASS_MAP: e = launch_map(p, in, out, ws, st); break;
         default: return MCLAHE_ERR_INVALID_ARG;
     }
@@ -261,9 +264,8 @@ int mclahe_pass_launches(mclahe_plan_t p, mclahe_pass pass) {
     if (!p) return 0;
     switch (pass) {
         case MCLAHE_PASS_RANGE:
-            return (p->g.mode == MCLAHE_RANGE_GLOBAL && p->g.has_range) ? 0 : 1;
+            return (p->g.mode == MCLAHE_RANGE_GLOBAL && !p->g.has_range) ? 1 : 0;
         case MCLAHE_PASS_HIST:
-        case MCLAHE_PASS_LUT:
         case MCLAHE_PASS_MAP: return 1;
         default: return 0;
     }

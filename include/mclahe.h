@@ -96,13 +96,15 @@ typedef struct {
     int64_t n_kernels;            /* K = prod(n) */
     int64_t kernel_voxels;        /* V = prod(b) */
     int64_t n_voxels;             /* prod(s) */
+    int64_t table_stride;         /* floats per mapping-table row in the workspace (>= n_bins;
+                                     entries past n_bins - 1 repeat it) */
     /* byte offsets inside the workspace (all 256-byte aligned) */
     size_t ws_status;             /* uint32 status word */
     size_t ws_range_keys;         /* uint32 [2 or 2K] order-preserving min/max keys */
     size_t ws_hist;               /* uint32 [K][n_bins] kernel histograms */
     size_t ws_lo;                 /* float  [K] histogram range start per kernel */
     size_t ws_scale;              /* float  [K] histogram scale per kernel */
-    size_t ws_lut;                /* float  [K][n_bins] mapping tables */
+    size_t ws_lut;                /* float  [K][table_stride] mapping tables */
     size_t ws_scratch;            /* backward partials */
     size_t ws_bytes;              /* total workspace size */
 } mclahe_plan_info;

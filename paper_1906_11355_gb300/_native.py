@@ -50,7 +50,7 @@ class PlanInfo(ctypes.Structure):
         ("pad", ctypes.c_int64 * 4), ("pad_before", ctypes.c_int64 * 4),
         ("pad_after", ctypes.c_int64 * 4), ("n_kernels_dim", ctypes.c_int64 * 4),
         ("n_kernels", ctypes.c_int64), ("kernel_voxels", ctypes.c_int64),
-        ("n_voxels", ctypes.c_int64),
+        ("n_voxels", ctypes.c_int64), ("table_stride", ctypes.c_int64),
         ("ws_status", ctypes.c_size_t), ("ws_range_keys", ctypes.c_size_t),
         ("ws_hist", ctypes.c_size_t), ("ws_lo", ctypes.c_size_t), ("ws_scale", ctypes.c_size_t),
         ("ws_lut", ctypes.c_size_t), ("ws_scratch", ctypes.c_size_t), ("ws_bytes", ctypes.c_size_t),

@@ -76,9 +76,11 @@ class MCLAHE:
         return h.view(self.n_kernels, self.n_bins).to(torch.int64) & 0xFFFFFFFF
 
     def tables(self):
-        """float32 [K, n_bins] mapping tables."""
-        return self._view("ws_lut", self.n_kernels * self.n_bins, torch.float32).view(
-            self.n_kernels, self.n_bins)
+        """float32 [K, n_bins] mapping tables (rows of table_stride floats in
+        the workspace, padded past n_bins with the last entry)."""
+        ls = int(self.info["table_stride"])
+        return self._view("ws_lut", self.n_kernels * ls, torch.float32).view(
+            self.n_kernels, ls)[:, :self.n_bins]
 
     def ranges(self):
         """(lo[K], scale[K]) histogram ranges of the kernels."""

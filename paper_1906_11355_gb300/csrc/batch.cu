@@ -1,10 +1,6 @@
 // batch.cu -- many volumes in one pass per phase (no counterpart in the paper).
 #include "mclahe_internal.cuh"
 
-namespace mclahe {
-void release_graph_cache(mclahe_plan_s *p) { (void)p; }
-}  // namespace mclahe
-
 extern "C" {
 
 size_t mclahe_batch_workspace_bytes(int n_vol, const mclahe_plan_t *plans) {
@@ -27,11 +23,4 @@ mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, float *d_ou
     return MCLAHE_ERR_UNSUPPORTED;
 }
 
-mclahe_status mclahe_backward(mclahe_plan_t plan, const float *d_in, const float *d_grad_out,
-                              void *d_ws, size_t ws_bytes, const float *d_clip, float *d_grad_lut,
-                              float *d_grad_clip, mclahe_stream_t stream) {
-    (void)plan; (void)d_in; (void)d_grad_out; (void)d_ws; (void)ws_bytes; (void)d_clip;
-    (void)d_grad_lut; (void)d_grad_clip; (void)stream;
-    return MCLAHE_ERR_UNSUPPORTED;
-}
 }

@@ -1,0 +1,324 @@
+// map_impl.cuh -- intensity mapping of one inter-kernel cell by multilinear
+// interpolation (Sec. III.C, Eq. (12)-(13); Algorithm 1, the interpolation
+// loop).  Included by the per-volume launcher (k_map.cu) and the batched
+// launcher (batch.cu).
+//
+// Voxels that share the same 2^D nearest kernels form an inter-kernel cell
+// (the dotted regions of Fig. 2).  A CTA takes one cell (or a chunk of its
+// rows), stages the 2^D neighbouring mapping tables in shared memory, then
+// streams its voxels with 128-bit loads and stores, four quads in flight per
+// thread.  Each voxel takes its bin under every neighbour's range (one bin for
+// a global range), reads the tables at those bins and blends them with the
+// Lagrange coefficients
+//   out = sum_i prod_j w_{i_j, j} * lut[k0 + i][bin_{k0+i}(x)],
+//   w_{1,j} = d_{j0} / b_j,  w_{0,j} = 1 - w_{1,j},
+// where d_{j0} = (x_j + p_j0) - (k0_j b_j + (b_j - 1) / 2) is the distance to
+// the lower kernel's centre: w_{1,j} = m / (2 b_j) with the integer
+// m = 2 (x_j + p_j0) - (b_j - 1) - 2 b_j k0_j in [0, 2 b_j).  The sums over
+// the corners run on packed f32x2 pairs.
+//
+// Shared-memory layout (bank-conflict-free gathers).  The bins of the voxels
+// of a warp are unrelated, so 32 lanes reading the same corner of 32 random
+// bins would hit random banks.  Each table index therefore owns one 128-byte
+// row of 32 slots, slot s holding corner s mod 2^D (32 / 2^D copies of the
+// 2^D corner values), and lane l reads, at step t, the corner (t + l) mod 2^D
+// from copy l / 2^D: at every step the 32 lanes touch 32 different banks
+// whatever their bins.  With a global range the reads are 16-byte corner
+// quads and the rule applies per 8-lane phase.  The lane-dependent corner
+// order is undone by per-lane rotated copies of the corner ranges and
+// weights, built once per CTA and per row.  Tables too large for this layout
+// (more than 1280 entries) use one row of 2^D values per index.
+#pragma once
+
+#include "mclahe_internal.cuh"
+
+namespace mclahe {
+
+// Rotate an array of N values left by r (0 <= r < N, N a power of two) with
+// log2(N) levels of selects, keeping every index static.
+template <int N, typename T>
+__device__ __forceinline__ void rotate_left(T (&a)[N], int r) {
+#pragma unroll
+    for (int sh = 1; sh < N; sh <<= 1) {
+        const bool on = (r & sh) != 0;
+        T t[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) t[i] = on ? a[(i + sh) & (N - 1)] : a[i];
+#pragma unroll
+        for (int i = 0; i < N; ++i) a[i] = t[i];
+    }
+}
+
+// The replicated layout needs 128 bytes per table index.
+__host__ __device__ inline bool map_repl_fits(int P) { return size_t(P) * 128 <= 160 * 1024; }
+__host__ __device__ inline size_t map_smem_for(int D, int P) {
+    return map_repl_fits(P) ? size_t(P) * 128 : (size_t(1) << D) * size_t(P) * sizeof(float);
+}
+
+__device__ __forceinline__ void sts128(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+template <int D, bool ADAPTIVE, bool REPL>
+__device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict__ in,
+                                         float *__restrict__ out, const float *__restrict__ lut,
+                                         const float *__restrict__ lo_k,
+                                         const float *__restrict__ scale_k, int64_t cell, int chunk,
+                                         int chunks, float *tab) {
+    constexpr int NC = 1 << D;          // corners
+    constexpr int NO = 1 << (D - 1);    // corners over dims 0..D-2
+    constexpr int NQ = NC >= 4 ? NC / 4 : 1;   // 16-byte corner quads per index
+    constexpr uint32_t RSB = REPL ? 128u : uint32_t(4 * NC);   // bytes per table index
+    __shared__ float s_nlo[NC], s_sc[NC];
+    const int P = g.P, LS = g.LS;
+    const int lane = threadIdx.x & 31;
+
+    int cc[kMaxDim];
+    {
+        int64_t r = cell;
+#pragma unroll
+        for (int j = D - 1; j >= 0; --j) {
+            cc[j] = int(r % (g.d[j].n - 1));
+            r /= (g.d[j].n - 1);
+        }
+    }
+    // kernel index of corner i (bit D-1-d of i = side along dim d)
+    int64_t kbase = 0, kstr[kMaxDim];
+    {
+        int64_t st = 1;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            kstr[d] = st;
+            kbase += int64_t(cc[d]) * st;
+            st *= g.d[d].n;
+        }
+    }
+    auto corner_kernel = [&](int i) {
+        int64_t k = kbase;
+#pragma unroll
+        for (int d = 0; d < D; ++d) k += ((i >> (D - 1 - d)) & 1) ? kstr[d] : 0;
+        return k;
+    };
+
+    // stage the corner tables
+    if (REPL) {
+        if (NC >= 4) {
+            // task (j, q): corners 4q..4q+3 of index j into every copy's quad q
+            for (int t = threadIdx.x; t < P * NQ; t += blockDim.x) {
+                const int j = t / NQ, q = t - j * NQ;
+                const float4 v = make_float4(__ldg(lut + corner_kernel(4 * q) * LS + j),
+                                             __ldg(lut + corner_kernel(4 * q + 1) * LS + j),
+                                             __ldg(lut + corner_kernel(4 * q + 2) * LS + j),
+                                             __ldg(lut + corner_kernel(4 * q + 3) * LS + j));
+#pragma unroll
+                for (int a = 0; a < 8 / NQ; ++a) sts128(tab + j * 32 + (a * NQ + q) * 4, v);
+            }
+        } else {
+            for (int j = threadIdx.x; j < P; j += blockDim.x) {
+                const float c0 = __ldg(lut + corner_kernel(0) * LS + j);
+                const float c1 = __ldg(lut + corner_kernel(1) * LS + j);
+#pragma unroll
+                for (int a = 0; a < 8; ++a) sts128(tab + j * 32 + a * 4, make_float4(c0, c1, c0, c1));
+            }
+        }
+    } else {
+        for (int t = threadIdx.x; t < NC * P; t += blockDim.x) {
+            const int j = t / NC, i = t - j * NC;
+            tab[t] = __ldg(lut + corner_kernel(i) * LS + j);
+        }
+    }
+    if (threadIdx.x < NC) {
+        const int64_t k = corner_kernel(threadIdx.x);
+        s_nlo[threadIdx.x] = -lo_k[k];
+        s_sc[threadIdx.x] = scale_k[k];
+    }
+
+    int box_lo[kMaxDim], len[kMaxDim];
+    int64_t stride[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        int a, b;
+        cell_range(g.d[j], cc[j], a, b);
+        box_lo[j] = a;
+        len[j] = b - a;
+        stride[j] = g.d[j].stride;
+    }
+    int R = 1;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) R *= len[j];
+    const int r0 = int((int64_t(R) * chunk) / chunks);
+    const int r1 = int((int64_t(R) * (chunk + 1)) / chunks);
+    __syncthreads();
+
+    // per-dim weight constants: w1 = float(2 x + mb_j) * inv2b_j
+    float inv2b[kMaxDim];
+    int mb[kMaxDim];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const Dim &dj = g.d[j];
+        inv2b[j] = 1.0f / float(2 * dj.b);
+        mb[j] = 2 * dj.p0 - (dj.b - 1) - 2 * dj.b * cc[j];
+    }
+    const uint32_t tab_s = uint32_t(__cvta_generic_to_shared(tab));
+    const float iqk = g.iqk, qkf = g.qkf;
+
+    // lane rotation (REPL): AHR reads corner (t + rot) mod NC at step t;
+    // GHR reads quad (s + rot) mod NQ at step s from copy (l / NQ) mod (8 / NQ)
+    const int rot = REPL ? (ADAPTIVE ? (lane & (NC - 1)) : (lane & (NQ - 1))) : 0;
+
+    // AHR: per step pair the two corners' ranges, per step the table address
+    constexpr int NA = ADAPTIVE ? NC : 1;
+    float2 anlo[ADAPTIVE ? NC / 2 : 1], asc[ADAPTIVE ? NC / 2 : 1];
+    uint32_t cbase[NA];
+    if (ADAPTIVE) {
+        float nl[NA], sc[NA];
+#pragma unroll
+        for (int t = 0; t < NA; ++t) {
+            const int c = REPL ? ((t + rot) & (NC - 1)) : t;
+            nl[t] = s_nlo[c];
+            sc[t] = s_sc[c];
+            const int slot = REPL ? ((lane & ~(NC - 1) & 31) | c) : c;
+            cbase[t] = tab_s + 4u * uint32_t(slot) - kBinBias * RSB;
+        }
+#pragma unroll
+        for (int t = 0; t < NA / 2; ++t) {
+            anlo[t] = make_float2(nl[2 * t], nl[2 * t + 1]);
+            asc[t] = make_float2(sc[2 * t], sc[2 * t + 1]);
+        }
+    }
+    const float gnlo = s_nlo[0], gsc = s_sc[0];
+    // GHR: table address of step s
+    uint32_t gbase[NQ];
+#pragma unroll
+    for (int s = 0; s < NQ; ++s) {
+        uint32_t off;
+        if (REPL) {
+            if (NC >= 4) {
+                const int qd = (s + rot) & (NQ - 1);
+                const int copy = (lane / NQ) & ((8 / NQ) - 1);
+                off = 16u * uint32_t(copy * NQ + qd);
+            } else {
+                off = 8u * uint32_t(lane & 15);
+            }
+        } else {
+            off = 16u * uint32_t(s);
+        }
+        gbase[s] = tab_s + off - kBinBias * RSB;
+    }
+
+    const int L = len[D - 1];
+    const int xl = box_lo[D - 1];
+    const bool same_align = (D == 1) || ((g.d[D >= 2 ? D - 2 : 0].stride & 3) == 0);
+    const float inv2b_l = inv2b[D - 1];
+    const int mb_l = mb[D - 1];
+
+    // Per-row state: the outer weights in the order this lane reads them.
+    //   AHR: w[t] = weight over dims 0..D-2 of corner (t + rot) mod NC, paired;
+    //   GHR: (wa[s], wb[s]) = outer weights of the two outer corners of quad
+    //        (s + rot) mod NQ (corners 4q..4q+3 = outer 2q, 2q+1 x last 0, 1).
+    struct MRow {
+        float2 w[ADAPTIVE ? NC / 2 : 2 * NQ];
+    };
+    auto row_fn = [&](const int *coords, int64_t, MRow &st) {
+        float wo[NO];
+#pragma unroll
+        for (int i = 0; i < NO; ++i) wo[i] = 1.0f;
+#pragma unroll
+        for (int j = 0; j < D - 1; ++j) {
+            const float w1 = float(2 * coords[j] + mb[j]) * inv2b[j];
+            const float w0 = 1.0f - w1;
+#pragma unroll
+            for (int i = 0; i < NO; ++i) wo[i] *= ((i >> (D - 2 - j)) & 1) ? w1 : w0;
+        }
+        if (ADAPTIVE) {
+            float a[NA];
+#pragma unroll
+            for (int c = 0; c < NA; ++c) a[c] = wo[c >> 1];
+            if (REPL) rotate_left<NA>(a, rot);
+#pragma unroll
+            for (int t = 0; t < NA / 2; ++t) st.w[t] = make_float2(a[2 * t], a[2 * t + 1]);
+        } else if (NC >= 4) {
+            float pa[NQ], pb[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                pa[q] = wo[2 * q];
+                pb[q] = wo[2 * q + 1];
+            }
+            if (REPL && NQ > 1) {
+                rotate_left<NQ>(pa, rot);
+                rotate_left<NQ>(pb, rot);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                st.w[2 * q] = make_float2(pa[q], pa[q]);
+                st.w[2 * q + 1] = make_float2(pb[q], pb[q]);
+            }
+        } else {
+            st.w[0] = make_float2(1.0f, 1.0f);
+            st.w[1] = st.w[0];
+        }
+    };
+
+    const int rodd = rot & 1;
+    auto quad_fn = [&](MRow &st, const QuadRef &q) {
+        if (!q.has) return;
+        const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+        const float fb = float(2 * (xl + q.e0) + mb_l);
+        float res[4];
+        uint32_t gb[4];
+        if (!ADAPTIVE) {
+            const float2 nl = make_float2(gnlo, gnlo), sc = make_float2(gsc, gsc);
+            const uint2 b01 = qbits2(make_float2(vals[0], vals[1]), nl, sc, iqk, qkf);
+            const uint2 b23 = qbits2(make_float2(vals[2], vals[3]), nl, sc, iqk, qkf);
+            gb[0] = b01.x;
+            gb[1] = b01.y;
+            gb[2] = b23.x;
+            gb[3] = b23.y;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float w1 = (fb + float(2 * e)) * inv2b_l;
+            float a0, a1;   // sums over the outer corners at last-dim side 0 and 1
+            if (ADAPTIVE) {
+                float2 acc = make_float2(0.0f, 0.0f);
+                const float2 xx = make_float2(vals[e], vals[e]);
+#pragma unroll
+                for (int t = 0; t < NA / 2; ++t) {
+                    const uint2 b = qbits2(xx, anlo[t], asc[t], iqk, qkf);
+                    const float v0 = lds_f32(b.x * RSB + cbase[2 * t]);
+                    const float v1 = lds_f32(b.y * RSB + cbase[2 * t + 1]);
+                    acc = __ffma2_rn(make_float2(v0, v1), st.w[t], acc);
+                }
+                // even steps read last-dim side rot & 1, odd steps the other
+                a0 = rodd ? acc.y : acc.x;
+                a1 = rodd ? acc.x : acc.y;
+            } else if (NC >= 4) {
+                float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int s = 0; s < NQ; ++s) {
+                    const float4 t4 = lds_f32x4(gb[e] * RSB + gbase[s]);
+                    acc = __ffma2_rn(make_float2(t4.x, t4.y), st.w[2 * s], acc);
+                    acc = __ffma2_rn(make_float2(t4.z, t4.w), st.w[2 * s + 1], acc);
+                }
+                a0 = acc.x;
+                a1 = acc.y;
+            } else {
+                const float2 t2 = lds_f32x2(gb[e] * RSB + gbase[0]);
+                a0 = t2.x;
+                a1 = t2.y;
+            }
+            res[e] = fmaf(w1, a1 - a0, a0);
+        }
+        if (q.e0 >= 0 && q.e0 + 4 <= L) {
+            __stcs(reinterpret_cast<float4 *>(out + q.a), make_float4(res[0], res[1], res[2], res[3]));
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int el = q.e0 + e;
+                if (el >= 0 && el < L) out[q.a + e] = res[e];
+            }
+        }
+    };
+
+    walk_box<D, (ADAPTIVE && D >= 3) ? 2 : 4, MRow>(in, nullptr, g.N, stride, box_lo, len, r0, r1, same_align, true, row_fn, quad_fn);
+}
+
+}  // namespace mclahe

@@ -13,6 +13,7 @@ namespace mclahe {
 constexpr int kMaxDim = 4;
 constexpr int kMaxBins = 4096;
 constexpr size_t kWsAlign = 256;
+constexpr int kMaxPieces = 5;     // constant-multiplicity pieces of a footprint per dim
 
 // Unsigned 32-bit division by a runtime constant d >= 1 with one multiply-high
 // (round-up method of Granlund and Montgomery, "Division by invariant integers
@@ -44,6 +45,12 @@ struct Dim {
 };
 
 // Everything a kernel needs about one volume; passed by value.
+//
+// Table geometry.  The bin quantiser (see qbits below) yields an index in
+// [0, qk], qk = the smallest power of two >= n_bins - 1, where every index
+// >= n_bins - 1 stands for the last bin.  Mapping tables are therefore stored
+// with P = qk + 1 entries (entries n_bins .. qk repeat entry n_bins - 1), in
+// rows of LS >= P floats (LS a multiple of 4).
 struct Geom {
     int32_t D;          // dimensionality, 1..4
     int32_t nb;         // n_bins
@@ -51,7 +58,11 @@ struct Geom {
     int32_t has_range;  // GHR with a caller-given range
     float range_lo, range_hi;
     float clip;         // plan's clip limit
-    int32_t pad_;
+    int32_t qk;         // power of two >= nb - 1
+    float qkf;          // qk as a float
+    float iqk;          // 1 / qk (exact)
+    int32_t P;          // table entries, qk + 1
+    int32_t LS;         // table row stride in floats, P rounded up to 4
     int64_t K;          // kernels
     int64_t V;          // voxels per kernel
     int64_t N;          // voxels of the original volume
@@ -61,15 +72,17 @@ struct Geom {
 // Launch shapes chosen by the heuristic or the autotuner.
 struct Tuning {
     int hist_threads;   // threads per histogram CTA
-    int hist_chunks;    // CTAs per kernel in the range/histogram passes
+    int hist_chunks;    // CTAs per kernel (cluster size) in the histogram pass
+    int hist_copies;    // lane copies of the shared-memory histogram (8, 16 or 32)
     int map_threads;    // threads per mapping CTA
     int map_chunks;     // CTAs per inter-kernel cell in the mapping pass
+    int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)
 };
 
 // Workspace layout (byte offsets, kWsAlign aligned).
 struct Layout {
     size_t status, keys, hist, lo, scale, lut, scratch, total;
-    size_t keys_count;  // uint32 keys (2 for GHR, 2K for AHR)
+    size_t keys_count;  // uint32 range keys (2: the global range)
     size_t scratch_bytes;
 };
 
@@ -80,7 +93,7 @@ struct mclahe_plan_s {
     mclahe::Tuning t;
     mclahe::Layout ws;
     int64_t pad[mclahe::kMaxDim];
-    void *graph_cache;  // batch-mode graph owned by the first plan of a batch
+    int tuned;          // launch shapes come from mclahe_autotune
 };
 
 namespace mclahe {
@@ -111,31 +124,54 @@ __device__ __forceinline__ float range_scale(float lo, float hi, int nb) {
     return (hi > lo) ? __fdiv_rn(float(nb), __fsub_rn(hi, lo)) : 0.0f;
 }
 
-// Bin quantiser: clamp(floor(fp32(fp32(x - lo) * scale)), 0, nb - 1), each
-// operation rounded to nearest with no contraction.  Clamping before the
-// floor gives the same integer because the bounds are integers; NaN goes to
-// bin 0.
-__device__ __forceinline__ int quantise(float x, float lo, float scale, float top) {
-    float y = __fmul_rn(__fsub_rn(x, lo), scale);
-    y = fminf(fmaxf(y, 0.0f), top);
-    return __float2int_rd(y);
-}
-
-// The same quantiser returning the bits of the float 2^23 + bin: after the
-// clamp, y lies in [0, nb - 1], where adding 2^23 rounded down is exactly
-// 2^23 + floor(y) (the float spacing there is 1).  Callers fold the constant
-// 0x4B000000 into their address arithmetic, which avoids the quarter-rate
-// float-to-int conversion.
+// ---------------------------------------------------------------------------
+// Bin quantiser.  The reading of the histogram step of Algorithm 1 is
+//   bin(x) = clamp(floor(y), 0, nb - 1),  y = fp32(fp32(x - lo) * scale),
+// each operation rounded to nearest.  It is evaluated as
+//   t = min(max(fp32(y * 2^-k), 0), 1)      (mul.rn.sat; exact scaling)
+//   bits = fp32_rd(t * 2^k + 2^23)          (one fma rounded down)
+// where 2^k = qk >= nb - 1.  Multiplying by a power of two is exact whenever
+// the result is a normal number, and when it is not, y < 1 and both forms give
+// index 0; so t * 2^k = clamp(y, 0, 2^k) exactly, and adding 2^23 rounded
+// down gives the float 2^23 + floor(clamp(y, 0, 2^k)), whose bits are
+// kBinBias + index with index in [0, qk].  Every index >= nb - 1 stands for
+// bin nb - 1 (tables are padded, histograms fold them).  NaN saturates to 0.
+// The pair form runs two values through the packed f32x2 instructions.
+// ---------------------------------------------------------------------------
 constexpr uint32_t kBinBias = 0x4B000000u;   // bits of 2^23
-__device__ __forceinline__ uint32_t quantise_bits(float x, float lo, float scale, float top) {
-    float y = __fmul_rn(__fsub_rn(x, lo), scale);
-    y = fminf(fmaxf(y, 0.0f), top);
-    return __float_as_uint(__fadd_rd(y, 8388608.0f));
+constexpr float kTwo23 = 8388608.0f;
+
+__device__ __forceinline__ float mul_sat(float a, float b) {
+    float r;
+    asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
 }
 
+struct QRange {
+    float nlo;     // -lo
+    float sc;      // scale
+};
+
+// Two values under two (possibly equal) ranges: returns kBinBias + index.
+__device__ __forceinline__ uint2 qbits2(float2 x, float2 nlo, float2 sc, float iqk, float qkf) {
+    float2 y = __fmul2_rn(__fadd2_rn(x, nlo), sc);
+    y.x = mul_sat(y.x, iqk);
+    y.y = mul_sat(y.y, iqk);
+    y = __ffma2_rd(y, make_float2(qkf, qkf), make_float2(kTwo23, kTwo23));
+    return make_uint2(__float_as_uint(y.x), __float_as_uint(y.y));
+}
+
+__device__ __forceinline__ uint32_t qbits1(float x, float nlo, float sc, float iqk, float qkf) {
+    float y = __fmul_rn(__fadd_rn(x, nlo), sc);
+    y = mul_sat(y, iqk);
+    return __float_as_uint(__fmaf_rd(y, qkf, kTwo23));
+}
+
+// ---------------------------------------------------------------------------
 // Footprint of kernel k along one dimension: the original indices whose
 // mirror images (Sec. III.B) fall in the padded interval [k*b, k*b + b).
 // Multiplicity = number of images of x in that interval (0..3).
+// ---------------------------------------------------------------------------
 struct Foot {
     int32_t lo, hi;          // union, [lo, hi)
     int32_t ml, mh;          // main image
@@ -179,6 +215,45 @@ __device__ __forceinline__ Foot footprint(const Dim &d, int k) {
     return f;
 }
 
+// The footprint split into intervals of constant nonzero multiplicity.
+struct Pieces {
+    int n;
+    int a[kMaxPieces], e[kMaxPieces], m[kMaxPieces];   // [a, e) with multiplicity m
+};
+
+__device__ __forceinline__ Pieces footprint_pieces(const Dim &d, int k) {
+    const Foot f = footprint(d, k);
+    int bp[8];
+    int nbp = 0;
+    const int cand[8] = {f.lo, f.hi, f.ml, f.mh, f.ll, f.lh, f.rl, f.rh};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int v = cand[i];
+        bool dup = v < f.lo || v > f.hi;
+        for (int j = 0; j < nbp; ++j) dup |= (bp[j] == v);
+        if (!dup) {
+            int j = nbp++;
+            while (j > 0 && bp[j - 1] > v) {   // insertion sort
+                bp[j] = bp[j - 1];
+                --j;
+            }
+            bp[j] = v;
+        }
+    }
+    Pieces p;
+    p.n = 0;
+    for (int i = 0; i + 1 < nbp; ++i) {
+        const int m = f.mult(bp[i]);
+        if (m > 0 && p.n < kMaxPieces) {
+            p.a[p.n] = bp[i];
+            p.e[p.n] = bp[i + 1];
+            p.m[p.n] = m;
+            ++p.n;
+        }
+    }
+    return p;
+}
+
 // Original-index range [lo, hi) of inter-kernel cell c along one dimension:
 // the voxels whose lower neighbouring kernel (largest k with centre
 // k*b + (b-1)/2 <= x + p0, Sec. III.C) is c.
@@ -220,11 +295,11 @@ struct RowIter {
 // ---------------------------------------------------------------------------
 // Row walker: the CTA visits rows [r0, r1) of a box (rows = all dims but the
 // last, each row L contiguous elements from element xl of the last dim) in
-// aligned 128-bit quads.  Every thread takes four quads per step, issuing the
-// four loads before using them:
-//   RU = 1: four quads of one row (lpr lanes share a row),
-//   RU = 2: two quads from each of two rows (rows of at most 2 quads),
-//   RU = 4: one quad from each of four rows (rows of 1 quad).
+// aligned 128-bit quads.  Every thread takes U quads per step (U = 2 or 4),
+// issuing the U loads before using them:
+//   RU = 1: U quads of one row (lpr lanes share a row),
+//   RU = 2: U/2 quads from each of two rows (rows of at most U/2 quads),
+//   RU = 4: one quad from each of four rows (U = 4, rows of 1 quad).
 // The step count is the same for all threads of the block, so warp-wide
 // primitives may be used inside.
 // ---------------------------------------------------------------------------
@@ -236,20 +311,18 @@ struct WalkShape {
     int G;      // row groups of the block (blockDim / lpr)
 };
 
-__device__ __forceinline__ WalkShape walk_shape(int L, int xl, bool same_align, int nthreads) {
+__device__ __forceinline__ WalkShape walk_shape(int L, int xl, bool same_align, int nthreads,
+                                                int U) {
     WalkShape w;
     w.Q = (((same_align ? (xl & 3) : 3) + L + 3) >> 2);
-    if (w.Q <= 1) {
-        w.ru = 4;
+    if (w.Q * 2 <= U) {
+        w.ru = U / w.Q >= 4 ? 4 : 2;   // Q = 1: U rows; Q = 2, U = 4: two rows
+        if (w.ru > U) w.ru = U;
         w.lpr = 1;
-        w.ql = 1;
-    } else if (w.Q == 2) {
-        w.ru = 2;
-        w.lpr = 1;
-        w.ql = 2;
+        w.ql = U / w.ru;
     } else {
         w.ru = 1;
-        const int want = (w.Q + 3) >> 2;
+        const int want = (w.Q + U - 1) / U;
         int lpr = 1;
         while (lpr < want && lpr < 32) lpr <<= 1;
         w.lpr = lpr;
@@ -264,6 +337,7 @@ __device__ __forceinline__ WalkShape walk_shape(int L, int xl, bool same_align, 
 // its element address.
 struct QuadRef {
     float4 v;
+    float4 v2;  // the same quad of the second input (walkers with two inputs)
     int e0;
     int64_t a;
     bool has;   // overlaps the row
@@ -287,13 +361,16 @@ __device__ __forceinline__ float4 load_quad4(const float *__restrict__ in, int64
 
 // Walks the rows of a box.  row_fn(const int *coords, int64_t row_start, S &state)
 // prepares per-row state S; quad_fn(S &state, const QuadRef &q) consumes one
-// quad.  Template parameter RU must equal shape.ru.
-template <int D, int RU, typename S, typename RowFn, typename QuadFn>
-__device__ __forceinline__ void walk_rows(const float *__restrict__ in, int64_t N,
+// quad.  Template parameter RU must equal shape.ru.  With TWO, the same quads
+// of a second array in2 (same layout) are loaded into QuadRef::v2.
+template <int D, int U, int RU, typename S, bool TWO, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_rows(const float *__restrict__ in,
+                                          const float *__restrict__ in2, int64_t N,
                                           const int64_t *stride, const int *box_lo,
                                           const int *box_len, int r0, int r1,
                                           const WalkShape &w, bool stream, RowFn row_fn,
                                           QuadFn quad_fn) {
+    constexpr int QPR = U / RU;   // quads per row and step (RU > 1)
     const int L = box_len[D - 1];
     const int xl = box_lo[D - 1];
     const int grp = threadIdx.x / w.lpr, gl = threadIdx.x & (w.lpr - 1);
@@ -320,28 +397,70 @@ __device__ __forceinline__ void walk_rows(const float *__restrict__ in, int64_t 
             row_fn(coords, s, st[ru]);
             it.next();
         }
-        const int qsteps = (RU == 1) ? (w.ql + 3) >> 2 : 1;
+        const int qsteps = (RU == 1) ? (w.ql + U - 1) / U : 1;
         for (int qs = 0; qs < qsteps; ++qs) {
-            QuadRef q[4];
+            QuadRef q[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int ru = (RU == 1) ? 0 : (RU == 2 ? (u >> 1) : u);
-                const int qi = (RU == 1) ? (gl + (qs * 4 + u) * w.lpr) : (RU == 2 ? (u & 1) : 0);
+            for (int u = 0; u < U; ++u) {
+                const int ru = (RU == 1) ? 0 : u / QPR;
+                const int qi = (RU == 1) ? (gl + (qs * U + u) * w.lpr) : (u % QPR);
                 const int64_t qbase = start[ru] & ~int64_t(3);
                 const int head = int(start[ru] - qbase);
                 q[u].e0 = 4 * qi - head;
                 q[u].a = qbase + 4 * int64_t(qi);
-                const bool inl = (RU == 1) ? ((qs * 4 + u) < w.ql) : true;
+                const bool inl = (RU == 1) ? ((qs * U + u) < w.ql) : true;
                 q[u].has = row_ok[ru] && inl && q[u].e0 < L && q[u].e0 + 4 > 0;
                 q[u].v = load_quad4(in, q[u].a, N, q[u].has, stream);
+                if (TWO) q[u].v2 = load_quad4(in2, q[u].a, N, q[u].has, true);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int ru = (RU == 1) ? 0 : (RU == 2 ? (u >> 1) : u);
+            for (int u = 0; u < U; ++u) {
+                const int ru = (RU == 1) ? 0 : u / QPR;
                 quad_fn(st[ru], q[u]);
             }
         }
     }
+}
+
+// Dispatch of walk_rows on the shape's RU.
+template <int D, int U, typename S, bool TWO = false, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_box(const float *__restrict__ in,
+                                         const float *__restrict__ in2, int64_t N,
+                                         const int64_t *stride, const int *box_lo,
+                                         const int *box_len, int r0, int r1, bool same_align,
+                                         bool stream, RowFn row_fn, QuadFn quad_fn) {
+    const WalkShape ws = walk_shape(box_len[D - 1], box_lo[D - 1], same_align, blockDim.x, U);
+    if (ws.ru == 1)
+        walk_rows<D, U, 1, S, TWO>(in, in2, N, stride, box_lo, box_len, r0, r1, ws, stream,
+                                   row_fn, quad_fn);
+    else if (U >= 4 && ws.ru == 4)
+        walk_rows<D, U, (U >= 4 ? 4 : 1), S, TWO>(in, in2, N, stride, box_lo, box_len, r0, r1, ws,
+                                                  stream, row_fn, quad_fn);
+    else
+        walk_rows<D, U, 2, S, TWO>(in, in2, N, stride, box_lo, box_len, r0, r1, ws, stream,
+                                   row_fn, quad_fn);
+}
+
+// shared-memory access by 32-bit shared-window address
+__device__ __forceinline__ void red_shared_add(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ float2 lds_f32x2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ float4 lds_f32x4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -353,18 +472,22 @@ cudaError_t launch_hist(const mclahe_plan_s &p, const float *in, unsigned char *
                         const float *d_clip, cudaStream_t st);
 cudaError_t launch_map(const mclahe_plan_s &p, const float *in, float *out,
                        const unsigned char *ws, cudaStream_t st);
+cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float *gout,
+                            unsigned char *ws, const float *d_clip, float *d_grad_lut,
+                            float *d_grad_clip, cudaStream_t st);
+size_t bwd_partial_floats(const Geom &g, int chunks);
+size_t hist_smem_bytes(const Geom &g, int copies);
+size_t map_smem_bytes(const Geom &g);
+bool map_replicated(const Geom &g);
 
 // plan.cu
 int device_sms();
 int64_t n_cells(const Geom &g);
 Tuning default_tuning(const Geom &g);
-Layout make_layout(const Geom &g);
+Layout make_layout(const Geom &g, const Tuning &t);
 mclahe_status check_forward_args(const mclahe_plan_s *p, const void *in, const void *out,
                                  const void *ws, size_t ws_bytes);
 mclahe_status forward_impl(const mclahe_plan_s &p, const float *in, float *out, unsigned char *ws,
                            const float *d_clip, cudaStream_t st);
-
-// batch.cu
-void release_graph_cache(mclahe_plan_s *p);
 
 }  // namespace mclahe

@@ -34,49 +34,58 @@ int64_t n_cells(const Geom &g) {
     return c;
 }
 
-// Default launch shapes: enough CTAs for several waves on 152 SMs, each
-// covering at least a few thousand voxels.
+// Default launch shapes (the autotuner may replace them).
+//   histogram: R lane copies, as many as keep the copy summation (P * R
+//   words per CTA) small next to the CTA's voxels and the shared memory at
+//   most 80 KiB; cluster size C, a power of two up to 8, grown while the
+//   grid is short of four CTAs per SM and every CTA keeps enough voxels;
+//   mapping: enough CTAs for several waves on the SMs, each covering at least
+//   four rows of its cell.
 Tuning default_tuning(const Geom &g) {
     Tuning t;
     t.hist_threads = 256;
     t.map_threads = 256;
-    const int64_t target = 152 * 8;
-    int64_t rows = 1;   // rows of an interior kernel footprint
+    const int sms = 152;
+    int R = 32;
+    while (R > 1 && (int64_t(g.P) * R > std::max<int64_t>(g.V / 2, g.P) ||
+                     hist_smem_bytes(g, R) > 80 * 1024))
+        R >>= 1;
+    t.hist_copies = R;
+    int C = 1;
+    while (C < 8 && g.K * C < 4 * sms && g.V / (2 * C) >= 2 * int64_t(g.P) * R) C <<= 1;
+    t.hist_chunks = C;
+    int64_t rows = 1;   // rows of an interior cell
     for (int j = 0; j + 1 < g.D; ++j) rows *= g.d[j].b;
-    // the CTAs of one kernel form a cluster (at most 8, the portable size)
-    int64_t hc = (target + g.K - 1) / g.K;
-    hc = std::min<int64_t>(std::max<int64_t>(hc, 1), std::max<int64_t>(rows / 4, 1));
-    int c = 1;
-    while (c < hc && c < 8) c <<= 1;
-    t.hist_chunks = c;
     const int64_t cells = n_cells(g);
-    int64_t mc = (target + cells - 1) / cells;
+    int64_t mc = (int64_t(sms) * 8 + cells - 1) / cells;
     mc = std::min<int64_t>(std::max<int64_t>(mc, 1), std::max<int64_t>(rows / 4, 1));
     t.map_chunks = int(std::min<int64_t>(mc, 64));
+    int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
+    bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
+    t.bwd_chunks = int(std::min<int64_t>(bc, 32));
     return t;
 }
 
-Layout make_layout(const Geom &g) {
+Layout make_layout(const Geom &g, const Tuning &t) {
     Layout L;
     size_t off = 0;
     L.status = off;
     off = align_up(off + sizeof(uint32_t) * 4);
-    L.keys_count = (g.mode == MCLAHE_RANGE_ADAPTIVE) ? size_t(2 * g.K) : 2;
+    L.keys_count = 2;
     L.keys = off;
     off = align_up(off + sizeof(uint32_t) * L.keys_count);
-    L.hist = off;                               // keys and hist are cleared together
+    L.hist = off;
     off = align_up(off + sizeof(uint32_t) * size_t(g.K) * g.nb);
     L.lo = off;
     off = align_up(off + sizeof(float) * size_t(g.K));
     L.scale = off;
     off = align_up(off + sizeof(float) * size_t(g.K));
     L.lut = off;
-    off = align_up(off + sizeof(float) * size_t(g.K) * g.nb);
-    // backward: per-cell partial table gradients (2^D corners x nb per cell)
-    // and per-kernel clip gradients
+    off = align_up(off + sizeof(float) * size_t(g.K) * g.LS);
+    // backward: partial table gradients (2^D corner tables per cell chunk)
+    // and per-kernel threshold gradients
     L.scratch = off;
-    L.scratch_bytes = sizeof(float) * size_t(n_cells(g)) * (size_t(1) << g.D) * g.nb +
-                      sizeof(float) * size_t(g.K);
+    L.scratch_bytes = sizeof(float) * bwd_partial_floats(g, t.bwd_chunks) + sizeof(float) * size_t(g.K);
     off = align_up(off + L.scratch_bytes);
     L.total = off;
     return L;
@@ -172,13 +181,22 @@ mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
         if (g.K > (int64_t(1) << 31) || g.V > (int64_t(1) << 31) || g.N > (int64_t(1) << 40))
             return MCLAHE_ERR_UNSUPPORTED;
     }
+    // table geometry of the bin quantiser: indices 0..qk, qk = 2^k >= nb - 1
+    g.qk = 1;
+    while (g.qk < n_bins - 1) g.qk <<= 1;
+    g.qkf = float(g.qk);
+    g.iqk = 1.0f / float(g.qk);
+    g.P = g.qk + 1;
+    g.LS = (g.P + 3) & ~3;
     int64_t stride = 1;
     for (int j = ndim - 1; j >= 0; --j) {
         g.d[j].stride = stride;
         stride *= g.d[j].s;
     }
-    // mapping tables of the 2^D neighbours must fit in shared memory
-    if ((size_t(1) << ndim) * size_t(n_bins) * sizeof(float) > 200 * 1024) return MCLAHE_ERR_UNSUPPORTED;
+    // the 2^D neighbouring tables and one histogram (one lane copy at the
+    // least) must fit in a CTA's shared memory
+    if (map_smem_bytes(g) > 200 * 1024 || hist_smem_bytes(g, 1) > 200 * 1024)
+        return MCLAHE_ERR_UNSUPPORTED;
     // CTAs per footprint row range: counts must stay in 32 bits
     int64_t foot = 1;
     for (int j = 0; j < ndim; ++j) foot *= std::min<int64_t>(g.d[j].s, 2 * int64_t(g.d[j].b));
@@ -189,16 +207,15 @@ mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
     std::memset(p, 0, sizeof(*p));
     p->g = g;
     p->t = default_tuning(g);
-    p->ws = make_layout(g);
+    p->ws = make_layout(g, p->t);
     for (int j = 0; j < kMaxDim; ++j) p->pad[j] = pad[j];
-    p->graph_cache = nullptr;
+    p->tuned = 0;
     *out = p;
     return MCLAHE_OK;
 }
 
 void mclahe_plan_destroy(mclahe_plan_t plan) {
     if (!plan) return;
-    release_graph_cache(plan);
     delete plan;
 }
 
@@ -221,6 +238,7 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->n_kernels = g.K;
     info->kernel_voxels = g.V;
     info->n_voxels = g.N;
+    info->table_stride = g.LS;
     info->ws_status = p->ws.status;
     info->ws_range_keys = p->ws.keys;
     info->ws_hist = p->ws.hist;

@@ -100,3 +100,41 @@ def mclahe(x, kernel_size, n_bins=256, clip_limit=0.01, adaptive=False, global_r
         op = MCLAHE(x.shape, kernel_size, n_bins, clip_limit, adaptive, global_range, x.device)
         _cache[key] = op
     return op.forward(x)
+
+
+class MCLAHEBatch:
+    """Many volumes of possibly different shapes, dimensionalities and
+    parameters in one call (mclahe_batch: one persistent launch per kind of
+    volume, optionally replayed from a captured CUDA graph).
+
+    specs: list of dicts with keys shape, kernel (kernel size), n_bins,
+    clip_limit, adaptive, and optionally global_range."""
+
+    def __init__(self, specs, device="cuda"):
+        self.specs = [dict(s) for s in specs]
+        self.plans = []
+        for s in self.specs:
+            mode = nat.MCLAHE_RANGE_ADAPTIVE if s.get("adaptive", False) else nat.MCLAHE_RANGE_GLOBAL
+            self.plans.append(nat.mclahe_plan(s["shape"], s["kernel"], s.get("n_bins", 256),
+                                              s.get("clip_limit", 0.01), mode, s.get("global_range")))
+        self.device = torch.device(device)
+        self.ws_bytes = nat.mclahe_batch_workspace_bytes(self.plans)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+
+    def forward(self, xs, outs=None, clip=None, stream=None, use_graph=True):
+        """Run MCLAHE on every volume of xs (contiguous float32 CUDA tensors);
+        returns outs.  clip: optional float32 CUDA tensor of one clip limit per
+        volume.  With use_graph, calls with the same tensors replay one graph."""
+        if len(xs) != len(self.plans):
+            raise ValueError("one input per plan expected")
+        for x, s in zip(xs, self.specs):
+            if x.device.type != "cuda" or x.dtype != torch.float32 or not x.is_contiguous():
+                raise ValueError("expected contiguous float32 CUDA tensors")
+            if tuple(x.shape) != tuple(s["shape"]):
+                raise ValueError(f"expected shape {tuple(s['shape'])}, got {tuple(x.shape)}")
+        if outs is None:
+            outs = [torch.empty_like(x) for x in xs]
+        nat.mclahe_batch(self.plans, xs, outs, self.ws, self.ws_bytes, clip, stream, use_graph)
+        return outs
+
+    __call__ = forward

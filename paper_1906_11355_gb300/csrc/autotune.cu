@@ -1,0 +1,138 @@
+// autotune.cu -- mclahe_autotune: pick the launch shapes of a plan's passes by
+// timing candidates on the caller's buffers (no counterpart in the paper).
+//
+// Histogram pass: cluster size C in {1, 2, 4, 8} x lane copies R in
+// {4, 8, 16, 32} (shared memory at most 120 KiB).  Mapping pass: CTAs per cell
+// in {1, 2, 4, ..., 64} (at most one row per CTA).  Each candidate runs twice
+// after one warm-up and keeps its faster time; results are cached per
+// (shape, kernel size, n_bins, range mode, given range) for the process, so a
+// later plan of the same problem takes them without timing.
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "mclahe_internal.cuh"
+
+namespace mclahe {
+
+mclahe_status run_pass(const mclahe_plan_s &p, int pass, const float *in, float *out,
+                       unsigned char *ws, const float *d_clip, cudaStream_t st);
+
+namespace {
+
+using TuneKey = std::tuple<int, std::vector<int64_t>, int, int, int>;
+std::mutex g_tune_mutex;
+std::map<TuneKey, Tuning> g_tuned;
+
+TuneKey tune_key(const mclahe_plan_s &p) {
+    std::vector<int64_t> dims;
+    for (int j = 0; j < p.g.D; ++j) {
+        dims.push_back(p.g.d[j].s);
+        dims.push_back(p.g.d[j].b);
+    }
+    return TuneKey(p.g.D, dims, p.g.nb, p.g.mode, p.g.has_range);
+}
+
+// Seconds of the best of two timed runs of one pass (after a warm-up), or a
+// negative value if a launch fails.
+float time_pass(mclahe_plan_s &p, int pass, const float *in, float *out, unsigned char *ws,
+                cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    if (run_pass(p, pass, in, out, ws, nullptr, st) != MCLAHE_OK) return -1.0f;
+    float best = 1e30f;
+    for (int r = 0; r < 2; ++r) {
+        cudaEventRecord(e0, st);
+        if (run_pass(p, pass, in, out, ws, nullptr, st) != MCLAHE_OK) return -1.0f;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = ms < best ? ms : best;
+    }
+    return best;
+}
+
+}  // namespace
+
+}  // namespace mclahe
+
+using namespace mclahe;
+
+extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, float *d_out,
+                                         void *d_ws, size_t ws_bytes, mclahe_stream_t stream) {
+    mclahe_status s = check_forward_args(p, d_in, d_out, d_ws, ws_bytes);
+    if (s != MCLAHE_OK) return s;
+    const TuneKey key = tune_key(*p);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            const int bwd = p->t.bwd_chunks;   // fixed by the workspace layout
+            p->t = it->second;
+            p->t.bwd_chunks = bwd;
+            p->tuned = 1;
+            return MCLAHE_OK;
+        }
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return MCLAHE_ERR_CUDA;
+    }
+    const Tuning t0 = p->t;
+    Tuning best = t0;
+    s = MCLAHE_OK;
+    // the range (if any) feeds the histogram pass
+    if (run_pass(*p, MCLAHE_PASS_CLEAR, d_in, d_out, ws, nullptr, st) != MCLAHE_OK ||
+        run_pass(*p, MCLAHE_PASS_RANGE, d_in, d_out, ws, nullptr, st) != MCLAHE_OK)
+        s = MCLAHE_ERR_CUDA;
+    float best_ms = 1e30f;
+    for (int C = 1; C <= 8 && s == MCLAHE_OK; C <<= 1) {
+        for (int R = 4; R <= 32; R <<= 1) {
+            if (hist_smem_bytes(p->g, R) > 120 * 1024) continue;
+            p->t.hist_chunks = C;
+            p->t.hist_copies = R;
+            const float ms = time_pass(*p, MCLAHE_PASS_HIST, d_in, d_out, ws, st, e0, e1);
+            if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.hist_chunks = C;
+                best.hist_copies = R;
+            }
+        }
+    }
+    cudaGetLastError();   // clear a failed candidate's launch error
+    if (s == MCLAHE_OK && best_ms >= 1e30f) s = MCLAHE_ERR_CUDA;
+    if (s == MCLAHE_OK) {
+        p->t = best;
+        // tables for the mapping candidates
+        if (run_pass(*p, MCLAHE_PASS_HIST, d_in, d_out, ws, nullptr, st) != MCLAHE_OK) s = MCLAHE_ERR_CUDA;
+        int64_t rows = 1;
+        for (int j = 0; j + 1 < p->g.D; ++j) rows *= p->g.d[j].b;
+        best_ms = 1e30f;
+        for (int mc = 1; mc <= 64 && mc <= rows && s == MCLAHE_OK; mc <<= 1) {
+            p->t.map_chunks = mc;
+            const float ms = time_pass(*p, MCLAHE_PASS_MAP, d_in, d_out, ws, st, e0, e1);
+            if (ms >= 0.0f && ms < best_ms) {
+                best_ms = ms;
+                best.map_chunks = mc;
+            }
+        }
+        cudaGetLastError();
+        if (best_ms >= 1e30f) s = MCLAHE_ERR_CUDA;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != MCLAHE_OK) {
+        p->t = t0;
+        return s;
+    }
+    p->t = best;
+    p->tuned = 1;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = best;
+    return MCLAHE_OK;
+}

@@ -78,7 +78,7 @@ __device__ __forceinline__ void clip_threshold(float c, int64_t V, int64_t &t_fl
 }
 
 __device__ __forceinline__ float load_clip(const float *d_clip, float plan_clip) {
-    float c = d_clip ? *d_clip : plan_clip;
+    float c = d_clip ? __ldcg(d_clip) : plan_clip;
     return fminf(fmaxf(c, 0.0f), 1.0f);   // NaN -> 0
 }
 
@@ -346,7 +346,7 @@ __device__ __forceinline__ void hist_kernel(const Geom &g, const float *__restri
             lo = g.range_lo;
             hi = g.range_hi;
         } else {
-            keys_to_range(keys[0], keys[1], lo, hi);
+            keys_to_range(__ldcg(keys), __ldcg(keys + 1), lo, hi);   // L2: may be this launch's
         }
         __syncthreads();   // bins zeroed
     }

@@ -3,6 +3,9 @@
 // loop).  Included by the per-volume launcher (k_map.cu) and the batched
 // launcher (batch.cu).
 //
+// Tables and ranges are read through L2 (ld.global.cg), so a batched launch
+// may map a volume whose tables were written earlier in the same launch.
+//
 // Voxels that share the same 2^D nearest kernels form an inter-kernel cell
 // (the dotted regions of Fig. 2).  A CTA takes one cell (or a chunk of its
 // rows), stages the 2^D neighbouring mapping tables in shared memory, then
@@ -104,17 +107,17 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             // task (j, q): corners 4q..4q+3 of index j into every copy's quad q
             for (int t = threadIdx.x; t < P * NQ; t += blockDim.x) {
                 const int j = t / NQ, q = t - j * NQ;
-                const float4 v = make_float4(__ldg(lut + corner_kernel(4 * q) * LS + j),
-                                             __ldg(lut + corner_kernel(4 * q + 1) * LS + j),
-                                             __ldg(lut + corner_kernel(4 * q + 2) * LS + j),
-                                             __ldg(lut + corner_kernel(4 * q + 3) * LS + j));
+                const float4 v = make_float4(__ldcg(lut + corner_kernel(4 * q) * LS + j),
+                                             __ldcg(lut + corner_kernel(4 * q + 1) * LS + j),
+                                             __ldcg(lut + corner_kernel(4 * q + 2) * LS + j),
+                                             __ldcg(lut + corner_kernel(4 * q + 3) * LS + j));
 #pragma unroll
                 for (int a = 0; a < 8 / NQ; ++a) sts128(tab + j * 32 + (a * NQ + q) * 4, v);
             }
         } else {
             for (int j = threadIdx.x; j < P; j += blockDim.x) {
-                const float c0 = __ldg(lut + corner_kernel(0) * LS + j);
-                const float c1 = __ldg(lut + corner_kernel(1) * LS + j);
+                const float c0 = __ldcg(lut + corner_kernel(0) * LS + j);
+                const float c1 = __ldcg(lut + corner_kernel(1) * LS + j);
 #pragma unroll
                 for (int a = 0; a < 8; ++a) sts128(tab + j * 32 + a * 4, make_float4(c0, c1, c0, c1));
             }
@@ -122,13 +125,13 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     } else {
         for (int t = threadIdx.x; t < NC * P; t += blockDim.x) {
             const int j = t / NC, i = t - j * NC;
-            tab[t] = __ldg(lut + corner_kernel(i) * LS + j);
+            tab[t] = __ldcg(lut + corner_kernel(i) * LS + j);
         }
     }
     if (threadIdx.x < NC) {
         const int64_t k = corner_kernel(threadIdx.x);
-        s_nlo[threadIdx.x] = -lo_k[k];
-        s_sc[threadIdx.x] = scale_k[k];
+        s_nlo[threadIdx.x] = -__ldcg(lo_k + k);
+        s_sc[threadIdx.x] = __ldcg(scale_k + k);
     }
 
     int box_lo[kMaxDim], len[kMaxDim];

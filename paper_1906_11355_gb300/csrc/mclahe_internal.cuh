@@ -480,6 +480,9 @@ size_t hist_smem_bytes(const Geom &g, int copies);
 size_t map_smem_bytes(const Geom &g);
 bool map_replicated(const Geom &g);
 
+// batch.cu
+void batch_forget_plan(const mclahe_plan_s *p);
+
 // plan.cu
 int device_sms();
 int64_t n_cells(const Geom &g);

@@ -216,6 +216,7 @@ mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
 
 void mclahe_plan_destroy(mclahe_plan_t plan) {
     if (!plan) return;
+    batch_forget_plan(plan);
     delete plan;
 }
 

@@ -1,0 +1,124 @@
+"""The batched form (mclahe_batch: persistent launches over a work list of
+kernel and cell tiles of many volumes, with per-volume ready counters) against
+the per-volume forward pass and the FP64 oracle.
+
+The batch runs the same per-kernel and per-cell code as mclahe_forward, so its
+histograms, tables and outputs must equal the per-volume results bit for bit,
+whatever the tile order; the oracle check keeps the usual 1e-5 bound."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1906_11355_gb300 import build
+
+    build.build()
+    return torch
+
+
+def _specs():
+    f = lambda c: float(np.float32(c))
+    return [
+        dict(shape=(96, 80), kernel=(12, 10), n_bins=256, clip_limit=f(0.01), adaptive=False),
+        dict(shape=(64, 48), kernel=(8, 6), n_bins=512, clip_limit=f(0.02), adaptive=False),
+        dict(shape=(40, 56), kernel=(5, 7), n_bins=64, clip_limit=f(0.03), adaptive=False,
+             global_range=(0.0, 4.0)),
+        dict(shape=(16, 40, 32), kernel=(2, 5, 4), n_bins=256, clip_limit=f(0.02), adaptive=True),
+        dict(shape=(24, 32, 40), kernel=(3, 4, 5), n_bins=512, clip_limit=f(0.02), adaptive=True),
+        dict(shape=(16, 16, 24, 8), kernel=(2, 2, 3, 1), n_bins=256, clip_limit=f(0.01), adaptive=False),
+        dict(shape=(8, 16, 16, 16), kernel=(1, 2, 2, 2), n_bins=512, clip_limit=f(0.01), adaptive=False),
+        dict(shape=(37,), kernel=(6,), n_bins=16, clip_limit=f(0.05), adaptive=True),
+    ]
+
+
+def _inputs(specs, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.gamma(2.0, 1.0, size=s["shape"]).astype(np.float32) for s in specs]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_per_volume_forward_and_oracle(torch_cuda, orc, use_graph):
+    torch = torch_cuda
+    from paper_1906_11355_gb300.api import MCLAHE, MCLAHEBatch
+
+    specs = _specs()
+    xs_h = _inputs(specs, 3)
+    xs = [torch.from_numpy(x).cuda() for x in xs_h]
+    batch = MCLAHEBatch(specs)
+    outs = batch.forward(xs, use_graph=use_graph)
+    for rep in range(2):   # a second call (graph replay) gives the same result
+        outs2 = batch.forward(xs, outs=[torch.empty_like(x) for x in xs], use_graph=use_graph)
+        torch.cuda.synchronize()
+        for a, b in zip(outs, outs2):
+            assert torch.equal(a, b)
+    from paper_1906_11355_gb300 import _native as nat
+
+    assert nat.mclahe_sync_status(batch.ws) == nat.MCLAHE_OK
+    for x, xh, s, out in zip(xs, xs_h, specs, outs):
+        op = MCLAHE(s["shape"], s["kernel"], s["n_bins"], s["clip_limit"], s["adaptive"],
+                    s.get("global_range"))
+        ref = op.forward(x)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), s
+        want = orc.mclahe(xh, s["kernel"], s["n_bins"], s["clip_limit"], mode=int(s["adaptive"]),
+                          range_=s.get("global_range"))
+        assert np.abs(out.cpu().numpy().astype(np.float64) - want).max() <= 1e-5, s
+
+
+def test_batch_per_volume_clip_and_new_data(torch_cuda, orc):
+    torch = torch_cuda
+    from paper_1906_11355_gb300.api import MCLAHEBatch
+
+    specs = _specs()[3:6]
+    batch = MCLAHEBatch(specs)
+    clips = np.array([0.005, 0.04, 0.2], np.float32)
+    clip = torch.from_numpy(clips).cuda()
+    xs = [torch.empty(s["shape"], device="cuda") for s in specs]
+    outs = [torch.empty_like(x) for x in xs]
+    for seed in (11, 12):   # same tensors (graph replay), new contents
+        xs_h = _inputs(specs, seed)
+        for x, xh in zip(xs, xs_h):
+            x.copy_(torch.from_numpy(xh))
+        batch.forward(xs, outs=outs, clip=clip)
+        torch.cuda.synchronize()
+        for xh, s, c, out in zip(xs_h, specs, clips, outs):
+            want = orc.mclahe(xh, s["kernel"], s["n_bins"], float(c), mode=int(s["adaptive"]))
+            assert np.abs(out.cpu().numpy().astype(np.float64) - want).max() <= 1e-5
+
+
+def test_batch_rejects_bad_arguments(torch_cuda):
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHEBatch
+
+    specs = _specs()[:2]
+    batch = MCLAHEBatch(specs)
+    xs = [torch.zeros(s["shape"], device="cuda") for s in specs]
+    with pytest.raises(nat.MclaheError) as e:
+        nat.mclahe_batch(batch.plans, xs, xs, batch.ws, batch.ws_bytes)   # in == out
+    assert e.value.status == nat.MCLAHE_ERR_INVALID_ARG
+    with pytest.raises(nat.MclaheError) as e:
+        nat.mclahe_batch(batch.plans, xs, [torch.empty_like(x) for x in xs], batch.ws, 256)
+    assert e.value.status == nat.MCLAHE_ERR_WORKSPACE
+
+
+def test_autotune_keeps_results_exact(torch_cuda, orc):
+    torch = torch_cuda
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    rng = np.random.default_rng(17)
+    x = rng.gamma(2.0, size=(32, 64, 64)).astype(np.float32)
+    op = MCLAHE(x.shape, (8, 16, 16), 256, float(np.float32(0.02)), adaptive=True)
+    xd = torch.from_numpy(x).cuda()
+    op.autotune(xd)
+    out = op.forward(xd)
+    torch.cuda.synchronize()
+    want, aux = orc.mclahe(x, (8, 16, 16), 256, float(np.float32(0.02)), mode=1, full=True)
+    np.testing.assert_array_equal(op.histograms().cpu().numpy(), aux["hist"].astype(np.int64))
+    assert np.abs(out.cpu().numpy() - want).max() <= 1e-5

@@ -47,7 +47,12 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default launch shapes (mclahe_autotune is skipped)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and forward+backward forms")
+    ap.add_argument("--form-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -141,20 +146,20 @@ class ClockSampler:
 # algorithmic bytes per launch of each pass (HBM roofline)
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(info, adaptive, has_range):
+    """Bytes each pass must move at least: the range pass reads the input once
+    (a global range not given by the caller); the histogram pass reads the
+    input once and writes the histograms, tables and ranges; the mapping pass
+    reads the input and writes the output (4 B per voxel each)."""
     N = info["n_voxels"]
     K = info["n_kernels"]
     nb = info["n_bins"]
-    D = info["ndim"]
-    # range: one read of the input (global range only; the adaptive ranges are
-    # found inside the histogram pass, which reads each voxel once from HBM);
-    # hist: input read + histogram and table writes; map: input read + output write
-    b = {
+    ls = info["table_stride"]
+    return {
         "range": 0 if (adaptive or has_range) else 4 * N,
-        "hist": 4 * N + 8 * K * nb + 8 * K,
+        "hist": 4 * N + 4 * K * nb + 4 * K * ls + 8 * K,
         "lut": 0,
         "map": 8 * N,
     }
-    return b
 
 
 def kernel_source_hash(pass_name):
@@ -253,6 +258,128 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# the batched and forward+backward forms, each against the plain forward
+# ---------------------------------------------------------------------------
+def _time_steps(fn, steps, warmup, stream, flush=None):
+    """Mean ms of fn() over `steps` calls timed with CUDA events on `stream`
+    (after `warmup` calls); flush() runs between steps, outside the events."""
+    import torch
+
+    for _ in range(warmup):
+        if flush is not None:
+            flush()
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def measure_batched(dev, steps, warmup):
+    """48 volumes of uneven shape (16 2-D, 24 3-D, 8 4-D; kernel 1/8 of each
+    extent, 256 or 512 bins) in one mclahe_batch call replayed from a CUDA
+    graph, against the same volumes run one mclahe_forward after another."""
+    import numpy as np
+    import torch
+
+    from paper_1906_11355_gb300 import synth
+    from paper_1906_11355_gb300.api import MCLAHE, MCLAHEBatch
+
+    specs = synth.batch_specs()
+    for s in specs:
+        s["clip_limit"] = float(np.float32(s["clip_limit"]))
+    xs = [synth.batch_volume_t(s, device=dev) for s in specs]
+    outs = [torch.empty_like(x) for x in xs]
+    voxels = sum(int(x.numel()) for x in xs)
+    stream = torch.cuda.current_stream(dev)
+    batch = MCLAHEBatch(specs, device=dev)
+    ms_batch = _time_steps(lambda: batch.forward(xs, outs=outs, use_graph=True), steps, warmup, stream)
+    ops = [MCLAHE(s["shape"], s["kernel"], s["n_bins"], s["clip_limit"], s["adaptive"], device=dev)
+           for s in specs]
+
+    def plain():
+        for op, x, o in zip(ops, xs, outs):
+            op.forward(x, out=o)
+
+    ms_plain = _time_steps(plain, steps, warmup, stream)
+    launches = {"plain": 0}
+    from paper_1906_11355_gb300 import _native as nat
+
+    for op in ops:
+        launches["plain"] += sum(nat.mclahe_pass_launches(op.plan, p) for p in range(nat.MCLAHE_N_PASSES))
+    groups = len({(len(s["shape"]), bool(s["adaptive"])) for s in specs})
+    del xs, outs, batch, ops
+    torch.cuda.empty_cache()
+    return {"workload": "batch-48-uneven-2d3d4d", "volumes": len(specs), "voxels": voxels,
+            "value": voxels / (ms_batch * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms_batch,
+            "plain_forward_ms": ms_plain, "plain_forward_value": voxels / (ms_plain * 1e-3) / 1e9,
+            "speedup_vs_plain_forward": ms_plain / ms_batch,
+            "launches": {"batched": groups, "plain_forward": launches["plain"]},
+            "data": "synthetic, drawn on the device (torch generators, seeds 1000+v)"}
+
+
+def measure_fwd_bwd(dev, steps, warmup):
+    """Forward + backward of 8 volumes 64x256x256 (fluorescence-like; kernel
+    16x64x64, 256 bins, adaptive range) with one learnable clip limit per
+    volume (U[0.005, 0.05]) and loss = mean squared error to a seeded target;
+    against the forward alone."""
+    import numpy as np
+    import torch
+
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300 import synth
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    B, shape, ks, nb = 8, (64, 256, 256), (16, 64, 64), 256
+    xs = [synth.fluorescence_t(shape, seed=2000 + v, device=dev) for v in range(B)]
+    tgt = [synth.fluorescence_t(shape, seed=3000 + v, device=dev) for v in range(B)]
+    tgt = [t / t.max() for t in tgt]
+    g = torch.Generator(device="cpu")
+    g.manual_seed(4)
+    clips = (0.005 + 0.045 * torch.rand(B, generator=g)).to(dev)
+    op = MCLAHE(shape, ks, nb, 0.02, adaptive=True, device=dev)
+    wss = [torch.empty(op.ws_bytes, dtype=torch.uint8, device=dev) for _ in range(B)]
+    outs = [torch.empty_like(x) for x in xs]
+    gouts = [torch.empty_like(x) for x in xs]
+    gclip = torch.empty(B, dtype=torch.float32, device=dev)
+    n = float(B * xs[0].numel())
+    stream = torch.cuda.current_stream(dev)
+
+    def fwd():
+        for v in range(B):
+            nat.mclahe_forward(op.plan, xs[v], outs[v], wss[v], op.ws_bytes, clips[v:v + 1], stream)
+
+    def fwd_bwd():
+        fwd()
+        for v in range(B):
+            torch.sub(outs[v], tgt[v], out=gouts[v]).mul_(2.0 / n)   # dL/d(out) of the MSE
+            nat.mclahe_backward(op.plan, xs[v], gouts[v], wss[v], op.ws_bytes, clips[v:v + 1], None,
+                                gclip[v:v + 1], stream)
+
+    ms_fwd = _time_steps(fwd, steps, warmup, stream)
+    ms_fb = _time_steps(fwd_bwd, steps, warmup, stream)
+    voxels = int(n)
+    out = {"workload": "fwd+bwd-8x64x256x256-learnable-clip", "voxels": voxels,
+           "value": voxels / (ms_fb * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms_fb,
+           "forward_ms": ms_fwd, "forward_value": voxels / (ms_fwd * 1e-3) / 1e9,
+           "fwd_bwd_over_fwd": ms_fb / ms_fwd,
+           "grad_clip_finite": bool(torch.isfinite(gclip).all().item()),
+           "data": "synthetic, drawn on the device (torch generators, seeds 2000+v, targets 3000+v)"}
+    del xs, tgt, wss, outs, gouts
+    torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
 def run_native(args):
@@ -281,6 +408,10 @@ def run_native(args):
                 adaptive=w["adaptive"], device=dev)
     x = torch.from_numpy(x_host).to(dev)
     out = torch.empty_like(x)
+    if not args.no_autotune:
+        op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
+    shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
+              if k in ("hist_group", "hist_cluster", "hist_copies", "map_chunks", "tuned")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     passes = list(range(nat.MCLAHE_N_PASSES))
@@ -373,6 +504,11 @@ def run_native(args):
         cpu = {"value": rate, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
                "sample": f"whole {args.workload} volume x{reps} ({el:.1f} s, FP64, OpenMP)"}
 
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = {"batched": measure_batched(dev, args.form_steps, 3),
+                 "fwd_bwd": measure_fwd_bwd(dev, args.form_steps, 3)}
+
     line = {
         "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -381,6 +517,7 @@ def run_native(args):
                    "n_bins": w["n_bins"], "clip_limit": w["clip_limit"],
                    "range": "adaptive" if w["adaptive"] else "global",
                    "l2": "flushed between steps (256 MiB write outside the step events)",
+                   "launch_shapes": shapes,
                    "voxels_per_gpu": voxels},
         "hbm_roofline_frac_whole_step": whole / peak,
         "passes_ms": pass_ms,
@@ -389,6 +526,7 @@ def run_native(args):
         "e2e": e2e,
         "gpu_launches": int(sum(launches.values()) * args.steps),
         "clocks": sampler.summary(t0, t1),
+        "forms": forms,
     }
     print(json.dumps(line))
     if world > 1:

@@ -107,6 +107,13 @@ typedef struct {
     size_t ws_lut;                /* float  [K][table_stride] mapping tables */
     size_t ws_scratch;            /* backward partials */
     size_t ws_bytes;              /* total workspace size */
+    /* launch shapes (defaults, or those picked by mclahe_autotune) */
+    int32_t hist_group;           /* kernels along the last dim per histogram work item */
+    int32_t hist_cluster;         /* CTAs (a thread-block cluster) per histogram work item */
+    int32_t hist_copies;          /* lane copies of the shared-memory histograms */
+    int32_t map_chunks;           /* CTAs per inter-kernel cell in the mapping pass */
+    int32_t bwd_chunks;           /* CTAs per inter-kernel cell in the backward pass */
+    int32_t tuned;                /* 1 if the shapes come from mclahe_autotune */
 } mclahe_plan_info;
 
 /*

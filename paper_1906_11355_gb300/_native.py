@@ -54,6 +54,9 @@ class PlanInfo(ctypes.Structure):
         ("ws_status", ctypes.c_size_t), ("ws_range_keys", ctypes.c_size_t),
         ("ws_hist", ctypes.c_size_t), ("ws_lo", ctypes.c_size_t), ("ws_scale", ctypes.c_size_t),
         ("ws_lut", ctypes.c_size_t), ("ws_scratch", ctypes.c_size_t), ("ws_bytes", ctypes.c_size_t),
+        ("hist_group", ctypes.c_int32), ("hist_cluster", ctypes.c_int32),
+        ("hist_copies", ctypes.c_int32), ("map_chunks", ctypes.c_int32),
+        ("bwd_chunks", ctypes.c_int32), ("tuned", ctypes.c_int32),
     ]
 
     def as_dict(self):

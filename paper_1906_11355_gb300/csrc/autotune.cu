@@ -1,8 +1,9 @@
 // autotune.cu -- mclahe_autotune: pick the launch shapes of a plan's passes by
 // timing candidates on the caller's buffers (no counterpart in the paper).
 //
-// Histogram pass: cluster size C in {1, 2, 4, 8} x lane copies R in
-// {4, 8, 16, 32} (shared memory at most 120 KiB).  Mapping pass: CTAs per cell
+// Histogram pass: kernels per work item G in {1, 2, 4, ...} and the whole
+// last dimension x cluster size C in {1, 2, 4, 8} x lane copies R in
+// {2, 4, 8, 16, 32} (shared memory at most 160 KiB).  Mapping pass: CTAs per cell
 // in {1, 2, 4, ..., 64} (at most one row per CTA).  Each candidate runs twice
 // after one warm-up and keeps its faster time; results are cached per
 // (shape, kernel size, n_bins, range mode, given range) for the process, so a
@@ -90,17 +91,25 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
         run_pass(*p, MCLAHE_PASS_RANGE, d_in, d_out, ws, nullptr, st) != MCLAHE_OK)
         s = MCLAHE_ERR_CUDA;
     float best_ms = 1e30f;
-    for (int C = 1; C <= 8 && s == MCLAHE_OK; C <<= 1) {
-        for (int R = 4; R <= 32; R <<= 1) {
-            if (hist_smem_bytes(p->g, R) > 120 * 1024) continue;
-            p->t.hist_chunks = C;
-            p->t.hist_copies = R;
-            const float ms = time_pass(*p, MCLAHE_PASS_HIST, d_in, d_out, ws, st, e0, e1);
-            if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.hist_chunks = C;
-                best.hist_copies = R;
+    std::vector<int> groups;
+    const int nl = p->g.d[p->g.D - 1].n;
+    for (int G = 1; G < nl; G <<= 1) groups.push_back(G);
+    groups.push_back(nl);
+    for (int G : groups) {
+        for (int C = 1; C <= 8 && s == MCLAHE_OK; C <<= 1) {
+            for (int R = 2; R <= 32; R <<= 1) {
+                if (hist_smem_bytes(p->g, R, G) > 160 * 1024) continue;
+                p->t.hist_group = G;
+                p->t.hist_chunks = C;
+                p->t.hist_copies = R;
+                const float ms = time_pass(*p, MCLAHE_PASS_HIST, d_in, d_out, ws, st, e0, e1);
+                if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best.hist_group = G;
+                    best.hist_chunks = C;
+                    best.hist_copies = R;
+                }
             }
         }
     }

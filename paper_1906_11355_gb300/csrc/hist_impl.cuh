@@ -11,21 +11,26 @@
 // sweep and added to its bin with that weight, which gives exactly the
 // histogram of the padded kernel.
 //
-// Phases of one cluster (kernel k); the cluster's CTAs split every box's rows:
-//   1. adaptive range only (Sec. III.D): min/max of the CTA's rows, exchanged
-//      across the cluster through distributed shared memory;
+// A work item is a group of G consecutive kernels along the last dimension
+// (see hist_group); its CTAs split every footprint box's rows.  Phases:
+//   1. adaptive range only (Sec. III.D): min/max of every kernel of the group
+//      over the CTA's rows, exchanged across the cluster through distributed
+//      shared memory;
 //   2. histogram sweep: 128-bit loads, the exact bin quantiser on packed f32x2
-//      pairs, and one shared-memory reduction per voxel into a histogram with
-//      R lane copies (lane l adds to copy l mod R; with R = 32 the 32 lanes of
-//      a warp always hit 32 different banks, whatever the data's skew);
-//   3. the copies are summed per bin (in staggered order, conflict-free), the
-//      padded indices >= n_bins - 1 folded into the last bin, and the CTAs'
-//      counts summed by cluster rank 0 through distributed shared memory in
-//      rank order (integers: exact and deterministic);
-//   4. rank 0 stores the histogram and turns it into the mapping table with
-//      the whole block (clip at T = clip * V, excess E spread as E / nb,
-//      cumulative sum, min-max normalisation), the clip decisions and prefix
-//      sums exact in integers.
+//      pairs, and one shared-memory reduction per voxel into its kernel's
+//      histogram, kept in R lane copies (lane l adds to copy l mod R; with
+//      R = 32 the lanes of a warp always hit different banks, whatever the
+//      data's skew).  Each thread owns fixed quad slots of every row (tile
+//      walker), so the kernel and weight of a slot are found once per box;
+//      quads that straddle kernels or mirror boundaries take a per-voxel path;
+//   3. the copies are summed per bin (in staggered order, conflict-free) and
+//      the padded indices >= n_bins - 1 folded into the last bin;
+//   4. cluster rank r owns kernels r, r + C, ... of the group: it sums the
+//      CTAs' counts in rank order through distributed shared memory (integers:
+//      exact and deterministic), stores the histogram and turns it into the
+//      mapping table with the whole block (clip at T = clip * V, excess E
+//      spread as E / nb, cumulative sum, min-max normalisation), the clip
+//      decisions and prefix sums exact in integers.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -215,209 +220,434 @@ __device__ __forceinline__ void block_lut(const uint32_t *h, int nb, int LS, int
     for (int j = nb + int(threadIdx.x); j < LS; j += blockDim.x) out[j] = st.flat ? 0.0f : 1.0f;
 }
 
-// Shared memory of one histogram CTA: R copies of P bins plus P counts.
-__host__ __device__ inline size_t hist_smem_words(int P, int R) { return size_t(P) * R + P; }
+// ---------------------------------------------------------------------------
+// Work item of the histogram pass: a group of G consecutive kernels along the
+// last (contiguous) dimension, at fixed kernel coordinates along the others.
+// Its footprint rows are contiguous runs of memory covering all G kernels, so
+// neighbouring kernels' voxels are read once, in whole sectors, by one item.
+// Shared memory of one CTA (32-bit words): R lane copies of the P padded bins
+// of every kernel of the group, the P counts of every kernel, and per kernel
+// its range keys and quantiser constants.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t hist_smem_words(int P, int R, int G) {
+    return size_t(G) * P * R + size_t(G) * P + 5 * size_t(G);
+}
+
+// Kernels (relative to kl0, among [kl0, kl1)) that hold an image of the
+// original index x along one dimension, with multiplicities (Sec. III.B: x
+// has its main image at x + p0 and mirror images at p0 - 1 - x for x < p0 and
+// at 2s - 1 - x + p0 for x >= s - p1).  Returns the number of distinct kernels.
+__device__ __forceinline__ int last_targets(const Dim &d, int x, int kl0, int kl1, int *kg, int *m) {
+    int P[3], np = 0;
+    P[np++] = x + d.p0;
+    if (x < d.p0) P[np++] = d.p0 - 1 - x;
+    if (x >= d.s - d.p1) P[np++] = 2 * d.s - 1 - x + d.p0;
+    int n = 0;
+    for (int i = 0; i < np; ++i) {
+        const int k = P[i] / d.b;
+        if (k < kl0 || k >= kl1) continue;
+        int j = 0;
+        while (j < n && kg[j] != k - kl0) ++j;
+        if (j == n) {
+            kg[n] = k - kl0;
+            m[n] = 0;
+            ++n;
+        }
+        m[j] += 1;
+    }
+    return n;
+}
+
+constexpr int kHistQmax = 4;   // quad slots per thread and row in the histogram pass
 
 template <int D, bool ADAPTIVE>
-__device__ __forceinline__ void hist_kernel(const Geom &g, const float *__restrict__ in,
-                                            const uint32_t *__restrict__ keys,
-                                            const float *__restrict__ d_clip,
-                                            uint32_t *__restrict__ hist, float *__restrict__ lut,
-                                            float *__restrict__ lo_out,
-                                            float *__restrict__ scale_out, int64_t k, int R,
-                                            uint32_t *sh) {
-    __shared__ float s_red[2][32];
-    __shared__ float s_mm[2];
+__device__ __forceinline__ void hist_group(const Geom &g, const float *__restrict__ in,
+                                           const uint32_t *__restrict__ keys,
+                                           const float *__restrict__ d_clip,
+                                           uint32_t *__restrict__ hist, float *__restrict__ lut,
+                                           float *__restrict__ lo_out,
+                                           float *__restrict__ scale_out, int64_t item, int G,
+                                           int R, uint32_t *sh) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = int(cluster.num_blocks());
     const int rank = int(cluster.block_rank());
     const int nb = g.nb, P = g.P;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *cnt = sh + size_t(P) * R;
+    const int lane = threadIdx.x & 31;
+    const Dim &dl = g.d[D - 1];
+    const int n_groups = (dl.n + G - 1) / G;
 
-    // kernel coordinates and the constant-multiplicity pieces of its footprint
-    Pieces pc[D];
-    int nsub = 1;
+    // item -> outer kernel coordinates and the group along the last dim
+    int kk[kMaxDim];
+    int64_t outer = item / n_groups;
+    const int grp = int(item - outer * n_groups);
     {
-        int64_t r = k;
-        int kk[kMaxDim];
+        int64_t r = outer;
 #pragma unroll
-        for (int j = D - 1; j >= 0; --j) {
+        for (int j = D - 2; j >= 0; --j) {
             kk[j] = int(r % g.d[j].n);
             r /= g.d[j].n;
         }
+    }
+    const int kl0 = grp * G, kl1 = min(kl0 + G, dl.n), GK = kl1 - kl0;
+    const int64_t kfirst = outer * dl.n + kl0;   // flat index of the group's first kernel
+
+    // smem: copies [G][P][R], counts [G][P], keys [2G], -lo [G], scale [G], lo [G]
+    uint32_t *cnt = sh + size_t(G) * P * R;
+    uint32_t *s_keys = cnt + size_t(G) * P;
+    float *s_nlo = reinterpret_cast<float *>(s_keys + 2 * G);
+    float *s_sc = s_nlo + G;
+    float *s_lo = s_sc + G;
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(sh);
+        const int nw = int(hist_smem_words(P, R, G));
+        for (int i = threadIdx.x; i < nw / 4; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
+        for (int i = (nw / 4) * 4 + threadIdx.x; i < nw; i += blockDim.x) sh[i] = 0;
+    }
+
+    // outer pieces (dims 0..D-2) and the last-dim extent of the group
+    Pieces pc[kMaxDim];
+    int nsub = 1;
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            pc[j] = footprint_pieces(g.d[j], kk[j]);
-            nsub *= pc[j].n;
-        }
+    for (int j = 0; j < D - 1; ++j) {
+        pc[j] = footprint_pieces(g.d[j], kk[j]);
+        nsub *= pc[j].n;
+    }
+    int xlo = dl.s, xhi = 0;
+    for (int k = kl0; k < kl1; ++k) {
+        const Foot f = footprint(dl, k);
+        xlo = min(xlo, f.lo);
+        xhi = max(xhi, f.hi);
     }
     int64_t stride[kMaxDim];
 #pragma unroll
     for (int j = 0; j < D; ++j) stride[j] = g.d[j].stride;
-    const bool same_align = (D == 1) || ((g.d[D >= 2 ? D - 2 : 0].stride & 3) == 0);
-
-    // visits every box of the footprint: fn(box_lo, box_len, weight, r0, r1)
+    const bool tiled = (dl.s & 3) == 0;   // every row starts at the same alignment
+    constexpr int kSeg = 4 * 32 * kHistQmax - 4;
+    // Visits every box: fn(box_lo, box_len, weight, r0, r1, kgfix).  With one
+    // kernel in the group the last dimension is cut into its constant-
+    // multiplicity pieces too, so every voxel of a box adds `weight` to
+    // kernel kgfix = 0; otherwise kgfix = -1 and the boxes are segments of
+    // the group's extent whose voxels are assigned to kernels quad by quad.
+    const bool single = GK == 1;
+    Pieces pl;
+    pl.n = 0;
+    if (single) pl = footprint_pieces(dl, kl0);
     auto for_boxes = [&](auto &&fn) {
         for (int sb = 0; sb < nsub; ++sb) {
             int box_lo[kMaxDim], len[kMaxDim];
             int w = 1, rest = sb, rows = 1;
 #pragma unroll
-            for (int j = D - 1; j >= 0; --j) {
+            for (int j = D - 2; j >= 0; --j) {
                 const int i = rest % pc[j].n;
                 rest /= pc[j].n;
                 box_lo[j] = pc[j].a[i];
                 len[j] = pc[j].e[i] - pc[j].a[i];
                 w *= pc[j].m[i];
-                if (j < D - 1) rows *= len[j];
+                rows *= len[j];
             }
             const int r0 = int((int64_t(rows) * rank) / C);
             const int r1 = int((int64_t(rows) * (rank + 1)) / C);
-            if (r1 > r0) fn(box_lo, len, w, r0, r1);
+            if (r1 <= r0) continue;
+            if (single) {
+                for (int i = 0; i < pl.n; ++i)
+                    for (int x0 = pl.a[i]; x0 < pl.e[i]; x0 += kSeg) {
+                        box_lo[D - 1] = x0;
+                        len[D - 1] = min(kSeg, pl.e[i] - x0);
+                        fn(box_lo, len, w * pl.m[i], r0, r1, 0);
+                    }
+            } else {
+                for (int x0 = xlo; x0 < xhi; x0 += kSeg) {   // segments along the last dim
+                    box_lo[D - 1] = x0;
+                    len[D - 1] = min(kSeg, xhi - x0);
+                    fn(box_lo, len, w, r0, r1, -1);
+                }
+            }
+        }
+    };
+    struct NoRow {};
+    auto no_row = [](const int *, NoRow &) {};
+    // every voxel of rows [r0, r1) of a box, one per thread at a time:
+    // fn(x along the last dim, value)
+    auto for_voxels = [&](const int *box_lo, const int *len, int r0, int r1, auto &&fn) {
+        const int L = len[D - 1];
+        const int64_t total = int64_t(r1 - r0) * L;
+        for (int64_t t = threadIdx.x; t < total; t += blockDim.x) {
+            const int r = r0 + int(t / L), e = int(t % L);
+            int rest = r;
+            int64_t a = box_lo[D - 1] + e;
+#pragma unroll
+            for (int j = D - 2; j >= 0; --j) {
+                int rr;
+                rest = small_div(rest, len[j], rr);
+                a += int64_t(box_lo[j] + rr) * stride[j];
+            }
+            fn(box_lo[D - 1] + e, __ldg(in + a));
         }
     };
 
-    {   // zero the copies and the counts
-        uint4 *z = reinterpret_cast<uint4 *>(sh);
-        const int n4 = int(hist_smem_words(P, R) / 4);
-        for (int i = threadIdx.x; i < n4; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
-        for (int i = n4 * 4 + threadIdx.x; i < int(hist_smem_words(P, R)); i += blockDim.x) sh[i] = 0;
-    }
-
-    struct NoRow {};
-    auto no_row = [](const int *, int64_t, NoRow &) {};
-
-    float lo, hi;
+    // ---- phase 1 (adaptive range only): min/max of every kernel of the group
     if (ADAPTIVE) {
-        // phase 1: min/max of this CTA's rows of the footprint
-        float mn = INFINITY, mx = -INFINITY;
-        for_boxes([&](const int *box_lo, const int *len, int, int r0, int r1) {
-            const int L = len[D - 1];
-            auto mm_quad = [&](NoRow &, const QuadRef &q) {
-                if (!q.has) return;
-                if (q.e0 >= 0 && q.e0 + 4 <= L) {
-                    mn = min3f(mn, q.v.x, q.v.y);
-                    mn = min3f(mn, q.v.z, q.v.w);
-                    mx = max3f(mx, q.v.x, q.v.y);
-                    mx = max3f(mx, q.v.z, q.v.w);
-                } else {
-                    const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+        auto key_min = [&](int kg, float v) { atomicMax(&s_keys[2 * kg], ~float_key(v)); };
+        auto key_max = [&](int kg, float v) { atomicMax(&s_keys[2 * kg + 1], float_key(v)); };
+        auto slow_elem = [&](int x, float v) {
+            int kg[3], m[3];
+            const int n = last_targets(dl, x, kl0, kl1, kg, m);
+            for (int t = 0; t < n; ++t) {
+                key_min(kg[t], v);
+                key_max(kg[t], v);
+            }
+        };
+        for_boxes([&](const int *box_lo, const int *len, int, int r0, int r1, int kgfix) {
+            const int L = len[D - 1], xs = box_lo[D - 1];
+            if (tiled) {
+                const TileShape ts = tile_shape(L, xs & 3, blockDim.x, kHistQmax);
+                struct MSlot {
+                    int kg;          // kernel of the group, -1: per-voxel path
+                    int q0;          // element offset of the slot in the row
+                    bool full;       // all four voxels inside the box
+                };
+                float mn[kHistQmax], mx[kHistQmax];
+                int tk[kHistQmax];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int el = q.e0 + e;
-                        if (el >= 0 && el < L) {
-                            mn = fminf(mn, vals[e]);
-                            mx = fmaxf(mx, vals[e]);
+                for (int i = 0; i < kHistQmax; ++i) {
+                    mn[i] = INFINITY;
+                    mx[i] = -INFINITY;
+                    tk[i] = -1;
+                }
+                auto slot = [&](int i, int e0) {
+                    MSlot sd{-1, e0, e0 >= 0 && e0 + 4 <= L};
+                    if (kgfix >= 0) {
+                        sd.kg = kgfix;
+                    } else if (sd.full) {
+                        // the targets change monotonically along x, so equal
+                        // single targets at both ends hold for the whole quad
+                        int kg0[3], m0[3], kg1[3], m1[3];
+                        if (last_targets(dl, xs + e0, kl0, kl1, kg0, m0) == 1 &&
+                            last_targets(dl, xs + e0 + 3, kl0, kl1, kg1, m1) == 1 && kg1[0] == kg0[0])
+                            sd.kg = kg0[0];
+                    }
+                    tk[i] = sd.full ? sd.kg : -1;
+                    return sd;
+                };
+                auto quad = [&](NoRow &, const MSlot &sd, int i, const float4 &v, const float4 &, int64_t) {
+                    if (sd.full && sd.kg >= 0) {
+                        mn[i] = min3f(mn[i], v.x, v.y);
+                        mn[i] = min3f(mn[i], v.z, v.w);
+                        mx[i] = max3f(mx[i], v.x, v.y);
+                        mx[i] = max3f(mx[i], v.z, v.w);
+                    } else {
+                        const float vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (sd.q0 + e < 0 || sd.q0 + e >= L) continue;
+                            if (sd.kg >= 0) {
+                                key_min(sd.kg, vals[e]);
+                                key_max(sd.kg, vals[e]);
+                            } else {
+                                slow_elem(xs + sd.q0 + e, vals[e]);
+                            }
                         }
                     }
-                }
-            };
-            walk_box<D, 4, NoRow>(in, nullptr, g.N, stride, box_lo, len, r0, r1, same_align, false, no_row,
-                               mm_quad);
-        });
+                };
+                walk_tile<D, kHistQmax, 4, NoRow, MSlot, false>(in, nullptr, stride, box_lo, len, r0, r1,
+                                                                ts, false, slot, no_row, quad);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if (lane == 0) {
-            s_red[0][warp] = mn;
-            s_red[1][warp] = mx;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < int(blockDim.x >> 5); ++w) {
-                mn = fminf(mn, s_red[0][w]);
-                mx = fmaxf(mx, s_red[1][w]);
+                for (int i = 0; i < kHistQmax; ++i)
+                    if (tk[i] >= 0 && mn[i] <= mx[i]) {
+                        key_min(tk[i], mn[i]);
+                        key_max(tk[i], mx[i]);
+                    }
+            } else {
+                // rows at varying alignments: voxel by voxel
+                for_voxels(box_lo, len, r0, r1, [&](int x, float v) {
+                    if (kgfix >= 0) {
+                        key_min(kgfix, v);
+                        key_max(kgfix, v);
+                    } else {
+                        slow_elem(x, v);
+                    }
+                });
             }
-            s_mm[0] = mn;
-            s_mm[1] = mx;
-        }
-        cluster.sync();   // every CTA's min/max (and zeroed bins) are visible
-        lo = INFINITY;
-        hi = -INFINITY;
-        for (int c = 0; c < C; ++c) {
-            const float *rm = cluster.map_shared_rank(s_mm, c);
-            lo = fminf(lo, rm[0]);
-            hi = fmaxf(hi, rm[1]);
+        });
+        cluster.sync();   // every CTA's keys are complete
+        for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
+            uint32_t a = 0, b = 0;
+            for (int c = 0; c < C; ++c) {
+                const uint32_t *rk = cluster.map_shared_rank(s_keys, c);
+                a = max(a, rk[2 * kg]);
+                b = max(b, rk[2 * kg + 1]);
+            }
+            float lo, hi;
+            keys_to_range(a, b, lo, hi);
+            s_lo[kg] = lo;
+            s_nlo[kg] = -lo;
+            s_sc[kg] = range_scale(lo, hi, nb);
         }
     } else {
+        float lo, hi;
         if (g.has_range) {
             lo = g.range_lo;
             hi = g.range_hi;
         } else {
             keys_to_range(__ldcg(keys), __ldcg(keys + 1), lo, hi);   // L2: may be this launch's
         }
-        __syncthreads();   // bins zeroed
+        for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
+            s_lo[kg] = lo;
+            s_nlo[kg] = -lo;
+            s_sc[kg] = range_scale(lo, hi, nb);
+        }
     }
-    const float scale = range_scale(lo, hi, nb);
+    __syncthreads();
 
-    // phase 2: histogram sweep, weight w per box
+    // ---- phase 2: histogram sweep
     {
         const uint32_t sh_base = uint32_t(__cvta_generic_to_shared(sh));
         const uint32_t r4 = uint32_t(4 * R);
-        const uint32_t base_l = sh_base + 4u * uint32_t(lane & (R - 1)) - kBinBias * r4;
-        const float2 nlo2 = make_float2(-lo, -lo), sc2 = make_float2(scale, scale);
+        const uint32_t lane_off = 4u * uint32_t(lane & (R - 1));
+        const uint32_t kstride = uint32_t(P) * r4;   // bytes per kernel's copies
         const float iqk = g.iqk, qkf = g.qkf;
-        for_boxes([&](const int *box_lo, const int *len, int w, int r0, int r1) {
-            const int L = len[D - 1];
+        auto add_elem = [&](int x, float v, uint32_t w) {
+            int kg[3], m[3];
+            const int n = last_targets(dl, x, kl0, kl1, kg, m);
+            for (int t = 0; t < n; ++t) {
+                const uint32_t b = qbits1(v, s_nlo[kg[t]], s_sc[kg[t]], iqk, qkf);
+                red_shared_add(sh_base + uint32_t(kg[t]) * kstride + lane_off + (b - kBinBias) * r4,
+                               w * uint32_t(m[t]));
+            }
+        };
+        for_boxes([&](const int *box_lo, const int *len, int w, int r0, int r1, int kgfix) {
+            const int L = len[D - 1], xs = box_lo[D - 1];
             const uint32_t wu = uint32_t(w);
-            auto hist_quad = [&](NoRow &, const QuadRef &q) {
-                if (!q.has) return;
-                const uint2 b01 = qbits2(make_float2(q.v.x, q.v.y), nlo2, sc2, iqk, qkf);
-                const uint2 b23 = qbits2(make_float2(q.v.z, q.v.w), nlo2, sc2, iqk, qkf);
-                const uint32_t bits[4] = {b01.x, b01.y, b23.x, b23.y};
-                if (q.e0 >= 0 && q.e0 + 4 <= L) {
+            if (tiled && kgfix >= 0) {
+                // every voxel of the box goes to kernel kgfix with weight w
+                const TileShape ts = tile_shape(L, xs & 3, blockDim.x, kHistQmax);
+                struct FSlot {
+                    int q0;          // element offset of the slot in the row
+                    bool full;       // all four voxels inside the box
+                };
+                const uint32_t base = sh_base + uint32_t(kgfix) * kstride + lane_off - kBinBias * r4;
+                const float2 n2 = make_float2(s_nlo[kgfix], s_nlo[kgfix]);
+                const float2 s2 = make_float2(s_sc[kgfix], s_sc[kgfix]);
+                auto slot = [&](int, int e0) { return FSlot{e0, e0 >= 0 && e0 + 4 <= L}; };
+                auto quad = [&](NoRow &, const FSlot &sd, int, const float4 &v, const float4 &, int64_t) {
+                    const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
+                    const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
+                    if (sd.full) {
+                        red_shared_add(b01.x * r4 + base, wu);
+                        red_shared_add(b01.y * r4 + base, wu);
+                        red_shared_add(b23.x * r4 + base, wu);
+                        red_shared_add(b23.y * r4 + base, wu);
+                    } else {
+                        const uint32_t bits[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) red_shared_add(bits[e] * r4 + base_l, wu);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int el = q.e0 + e;
-                        if (el >= 0 && el < L) red_shared_add(bits[e] * r4 + base_l, wu);
+                        for (int e = 0; e < 4; ++e)
+                            if (sd.q0 + e >= 0 && sd.q0 + e < L) red_shared_add(bits[e] * r4 + base, wu);
                     }
-                }
-            };
-            walk_box<D, 4, NoRow>(in, nullptr, g.N, stride, box_lo, len, r0, r1, same_align, false, no_row,
-                               hist_quad);
+                };
+                walk_tile<D, kHistQmax, 4, NoRow, FSlot, false>(in, nullptr, stride, box_lo, len, r0, r1,
+                                                                ts, false, slot, no_row, quad);
+            } else if (tiled) {
+                // groups of kernels: a slot's quad goes to one kernel (with
+                // one multiplicity) when its first and last voxel do -- the
+                // targets change monotonically along x -- else voxel by voxel
+                const TileShape ts = tile_shape(L, xs & 3, blockDim.x, kHistQmax);
+                struct HSlot {
+                    uint32_t base;   // copy address of bin 0 minus the bias; ~0: per-voxel path
+                    uint32_t w;      // weight of the slot's voxels
+                    int q0;          // element offset of the slot in the row
+                    float2 nl, sc;   // the kernel's quantiser constants (adaptive range)
+                };
+                auto slot = [&](int, int e0) {
+                    HSlot sd;
+                    sd.base = 0xffffffffu;
+                    sd.w = 0;
+                    sd.q0 = e0;
+                    sd.nl = make_float2(0.f, 0.f);
+                    sd.sc = sd.nl;
+                    if (e0 < 0 || e0 + 4 > L) return sd;
+                    int kg0[3], m0[3], kg1[3], m1[3];
+                    if (last_targets(dl, xs + e0, kl0, kl1, kg0, m0) != 1 ||
+                        last_targets(dl, xs + e0 + 3, kl0, kl1, kg1, m1) != 1 || kg1[0] != kg0[0] ||
+                        m1[0] != m0[0])
+                        return sd;
+                    sd.base = sh_base + uint32_t(kg0[0]) * kstride + lane_off - kBinBias * r4;
+                    sd.w = wu * uint32_t(m0[0]);
+                    if (ADAPTIVE) {
+                        sd.nl = make_float2(s_nlo[kg0[0]], s_nlo[kg0[0]]);
+                        sd.sc = make_float2(s_sc[kg0[0]], s_sc[kg0[0]]);
+                    }
+                    return sd;
+                };
+                const float2 gnl = make_float2(s_nlo[0], s_nlo[0]), gsc = make_float2(s_sc[0], s_sc[0]);
+                auto quad = [&](NoRow &, const HSlot &sd, int, const float4 &v, const float4 &, int64_t) {
+                    if (sd.base != 0xffffffffu) {
+                        const float2 n2 = ADAPTIVE ? sd.nl : gnl, s2 = ADAPTIVE ? sd.sc : gsc;
+                        const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
+                        const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
+                        red_shared_add(b01.x * r4 + sd.base, sd.w);
+                        red_shared_add(b01.y * r4 + sd.base, sd.w);
+                        red_shared_add(b23.x * r4 + sd.base, sd.w);
+                        red_shared_add(b23.y * r4 + sd.base, sd.w);
+                    } else {
+                        const float vals[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (sd.q0 + e >= 0 && sd.q0 + e < L) add_elem(xs + sd.q0 + e, vals[e], wu);
+                    }
+                };
+                walk_tile<D, kHistQmax, 4, NoRow, HSlot, false>(in, nullptr, stride, box_lo, len, r0, r1,
+                                                                ts, false, slot, no_row, quad);
+            } else {
+                // rows at varying alignments: voxel by voxel
+                for_voxels(box_lo, len, r0, r1, [&](int x, float v) {
+                    if (kgfix >= 0) {
+                        const uint32_t b = qbits1(v, s_nlo[kgfix], s_sc[kgfix], iqk, qkf);
+                        red_shared_add(sh_base + uint32_t(kgfix) * kstride + lane_off + (b - kBinBias) * r4, wu);
+                    } else {
+                        add_elem(x, v, wu);
+                    }
+                });
+            }
         });
     }
     __syncthreads();
 
-    // phase 3: sum the copies (copy (c + j) mod R of bin j at step c: the
+    // ---- phase 3: sum the copies (copy (c + j) mod R of bin j at step c: the
     // threads of a warp read different banks), fold the padded indices
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        const uint32_t *row = sh + size_t(j) * R;
+    for (int t = threadIdx.x; t < GK * P; t += blockDim.x) {
+        const int j = t % P;
+        const uint32_t *row = sh + size_t(t) * R;
         uint32_t s = 0;
         for (int c = 0; c < R; ++c) s += row[(c + j) & (R - 1)];
-        cnt[j] = s;
+        cnt[t] = s;
     }
     __syncthreads();
-    for (int j = nb + int(threadIdx.x); j < P; j += blockDim.x) atomicAdd(&cnt[nb - 1], cnt[j]);
-    if (C > 1) {
-        cluster.sync();   // every CTA's counts are complete
-        if (rank == 0) {
-            for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-                uint32_t s = cnt[j];
-                for (int c = 1; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[j];
-                cnt[j] = s;
-            }
-        }
-        cluster.sync();   // rank 0 has read the other CTAs' shared memory
-    } else {
-        __syncthreads();
+    for (int t = threadIdx.x; t < GK * (P - nb); t += blockDim.x) {
+        const int kg = t / (P - nb), j = nb + t % (P - nb);
+        atomicAdd(&cnt[kg * P + nb - 1], cnt[kg * P + j]);
     }
+    cluster.sync();   // every CTA's counts are complete
 
-    // phase 4: rank 0 stores the histogram and builds the mapping table
-    if (rank == 0) {
+    // ---- phase 4: rank r owns kernels r, r + C, ...: sums the CTAs' counts
+    // in rank order, stores the histogram, builds the mapping table
+    for (int kg = rank; kg < GK; kg += C) {
+        uint32_t *ck = cnt + size_t(kg) * P;
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+            uint32_t s = 0;
+            for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
+            ck[j] = s;
+        }
+        __syncthreads();
+        const int64_t k = kfirst + kg;
         uint32_t *gh = hist + k * nb;
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) gh[j] = cnt[j];
-        block_lut(cnt, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut + k * g.LS);
+        for (int j = threadIdx.x; j < nb; j += blockDim.x) gh[j] = ck[j];
+        block_lut(ck, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut + k * g.LS);
         if (threadIdx.x == 0) {
-            lo_out[k] = lo;
-            scale_out[k] = scale;
+            lo_out[k] = s_lo[kg];
+            scale_out[k] = s_sc[kg];
         }
     }
+    cluster.sync();   // the other CTAs' shared memory is no longer read
 }
 
 }  // namespace mclahe

@@ -261,11 +261,10 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     };
 
     const int rodd = rot & 1;
-    auto quad_fn = [&](MRow &st, const QuadRef &q) {
-        if (!q.has) return;
-        const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
-        const float fb = float(2 * (xl + q.e0) + mb_l);
-        float res[4];
+    const float two_inv2b = 2.0f * inv2b_l;
+    // the mapping of the four voxels of a quad (vals) at last-dim weight
+    // w1 = fbi + e * two_inv2b for voxel e
+    auto map4 = [&](const MRow &st, const float (&vals)[4], float fbi, float (&res)[4]) {
         uint32_t gb[4];
         if (!ADAPTIVE) {
             const float2 nl = make_float2(gnlo, gnlo), sc = make_float2(gsc, gsc);
@@ -278,7 +277,7 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const float w1 = (fb + float(2 * e)) * inv2b_l;
+            const float w1 = fmaf(float(e), two_inv2b, fbi);
             float a0, a1;   // sums over the outer corners at last-dim side 0 and 1
             if (ADAPTIVE) {
                 float2 acc = make_float2(0.0f, 0.0f);
@@ -310,18 +309,51 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             }
             res[e] = fmaf(w1, a1 - a0, a0);
         }
-        if (q.e0 >= 0 && q.e0 + 4 <= L) {
-            __stcs(reinterpret_cast<float4 *>(out + q.a), make_float4(res[0], res[1], res[2], res[3]));
+    };
+    auto store4 = [&](int64_t a, int e0, const float (&res)[4]) {
+        if (e0 >= 0 && e0 + 4 <= L) {
+            __stcs(reinterpret_cast<float4 *>(out + a), make_float4(res[0], res[1], res[2], res[3]));
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int el = q.e0 + e;
-                if (el >= 0 && el < L) out[q.a + e] = res[e];
-            }
+            for (int e = 0; e < 4; ++e)
+                if (e0 + e >= 0 && e0 + e < L) out[a + e] = res[e];
         }
     };
 
-    walk_box<D, (ADAPTIVE && D >= 3) ? 2 : 4, MRow>(in, nullptr, g.N, stride, box_lo, len, r0, r1, same_align, true, row_fn, quad_fn);
+    if ((g.d[D - 1].s & 3) == 0) {
+        // every row starts at the same alignment: fixed quad slots per thread
+        constexpr int QM = 4;
+        struct MSlot {
+            float fbi;   // last-dim weight w1 of the slot's first voxel
+            int e0;
+        };
+        const TileShape ts = tile_shape(L, xl & 3, blockDim.x, QM);
+        auto slot = [&](int, int e0) {
+            MSlot sd;
+            sd.e0 = e0;
+            sd.fbi = float(2 * (xl + e0) + mb_l) * inv2b_l;
+            return sd;
+        };
+        auto row2 = [&](const int *coords, MRow &st) { row_fn(coords, 0, st); };
+        auto quad = [&](MRow &st, const MSlot &sd, int, const float4 &v, const float4 &, int64_t a) {
+            const float vals[4] = {v.x, v.y, v.z, v.w};
+            float res[4];
+            map4(st, vals, sd.fbi, res);
+            store4(a, sd.e0, res);
+        };
+        walk_tile<D, QM, (ADAPTIVE && D >= 3) ? 2 : 4, MRow, MSlot, false>(
+            in, nullptr, stride, box_lo, len, r0, r1, ts, true, slot, row2, quad);
+    } else {
+        auto quad_fn = [&](MRow &st, const QuadRef &q) {
+            if (!q.has) return;
+            const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+            float res[4];
+            map4(st, vals, float(2 * (xl + q.e0) + mb_l) * inv2b_l, res);
+            store4(q.a, q.e0, res);
+        };
+        walk_box<D, (ADAPTIVE && D >= 3) ? 2 : 4, MRow>(in, nullptr, g.N, stride, box_lo, len, r0, r1,
+                                                        same_align, true, row_fn, quad_fn);
+    }
 }
 
 }  // namespace mclahe

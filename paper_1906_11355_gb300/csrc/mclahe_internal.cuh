@@ -73,7 +73,8 @@ struct Geom {
 struct Tuning {
     int hist_threads;   // threads per histogram CTA
     int hist_chunks;    // CTAs per kernel (cluster size) in the histogram pass
-    int hist_copies;    // lane copies of the shared-memory histogram (8, 16 or 32)
+    int hist_copies;    // lane copies of the shared-memory histograms (1 .. 32)
+    int hist_group;     // kernels along the last dimension per histogram work item
     int map_threads;    // threads per mapping CTA
     int map_chunks;     // CTAs per inter-kernel cell in the mapping pass
     int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)
@@ -222,6 +223,17 @@ struct Pieces {
 };
 
 __device__ __forceinline__ Pieces footprint_pieces(const Dim &d, int k) {
+    Pieces p;
+    {   // interior kernel: one piece, the main image, multiplicity 1
+        const int a = k * d.b - d.p0;
+        if (a >= 0 && a + d.b <= d.s) {
+            p.n = 1;
+            p.a[0] = a;
+            p.e[0] = a + d.b;
+            p.m[0] = 1;
+            return p;
+        }
+    }
     const Foot f = footprint(d, k);
     int bp[8];
     int nbp = 0;
@@ -240,7 +252,6 @@ __device__ __forceinline__ Pieces footprint_pieces(const Dim &d, int k) {
             bp[j] = v;
         }
     }
-    Pieces p;
     p.n = 0;
     for (int i = 0; i + 1 < nbp; ++i) {
         const int m = f.mult(bp[i]);
@@ -264,8 +275,25 @@ __device__ __forceinline__ void cell_range(const Dim &d, int c, int &lo, int &hi
     hi = min(max(hi, 0), d.s);
 }
 
+// Quotient and remainder of small non-negative integers (a < 2^24, 1 <= d <
+// 2^24) through a float reciprocal, corrected to the exact integer result.
+__device__ __forceinline__ int small_div(int a, int d, int &rem) {
+    int q = __float2int_rz(__int2float_rz(a) * __frcp_rn(__int2float_rn(d)));
+    int r = a - q * d;
+    if (r < 0) {
+        q -= 1;
+        r += d;
+    } else if (r >= d) {
+        q += 1;
+        r -= d;
+    }
+    rem = r;
+    return q;
+}
+
 // Iterator over the rows (all dims but the last) of a box, advancing by a
-// fixed number of rows each step (mixed-radix add with carry).
+// fixed number of rows each step (mixed-radix add with carry).  Row indices
+// stay below 2^24 (the plan bounds a footprint's rows).
 template <int D>
 struct RowIter {
     int c[kMaxDim];     // coordinates inside the box, dims 0..D-2
@@ -275,10 +303,11 @@ struct RowIter {
 #pragma unroll
         for (int j = D - 2; j >= 0; --j) {
             len[j] = box_len[j];
-            c[j] = start % len[j];
-            start /= len[j];
-            adv[j] = step % len[j];
-            step /= len[j];
+            int r;
+            start = small_div(start, len[j], r);
+            c[j] = r;
+            step = small_div(step, len[j], r);
+            adv[j] = r;
         }
     }
     __device__ __forceinline__ void next() {
@@ -441,6 +470,95 @@ __device__ __forceinline__ void walk_box(const float *__restrict__ in,
                                    row_fn, quad_fn);
 }
 
+// ---------------------------------------------------------------------------
+// Tile walker: for a box whose rows all start at the same alignment mod 4
+// (the row stride a multiple of 4, or a single row), every thread owns fixed
+// quad slots of every row it visits: LPR lanes share a row, lane gl takes the
+// quads gl, gl + LPR, ..., gl + (QL - 1) LPR of it.  A slot's position in the
+// row, and so its masks and anything the consumer derives from it, is the
+// same in every row; slot_fn(i, e0) runs once per slot (e0 = element offset
+// of the slot's first element in the row, possibly negative) and returns the
+// slot's data SD, row_fn(coords, state) runs once per row, and
+// quad_fn(state, slot data, i, v, v2, a) once per loaded quad (a = element
+// address of the quad's first element).  Loads are issued
+// U at a time; every loop is unrolled, so slot data stay in registers.  QL <= QMAX is required: boxes with rows longer
+// than 4 * 32 * QMAX - 3 elements must be split along the last dimension.
+// ---------------------------------------------------------------------------
+struct TileShape {
+    int head;   // first row element's offset in its aligned quad
+    int Q;      // quads per row
+    int LPR;    // lanes per row (power of two <= 32)
+    int QL;     // quads per lane per row
+    int G;      // rows in flight per block
+};
+
+__device__ __forceinline__ TileShape tile_shape(int L, int head, int nthreads, int qmax) {
+    TileShape t;
+    t.head = head;
+    t.Q = (head + L + 3) >> 2;
+    int lpr = 1;
+    while (lpr < 32 && lpr * qmax < t.Q) lpr <<= 1;
+    t.LPR = lpr;
+    t.QL = (t.Q + lpr - 1) / lpr;
+    t.G = nthreads / lpr;
+    return t;
+}
+
+template <int D, int QMAX, int U, typename S, typename SD, bool TWO, typename SlotFn,
+          typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_tile(const float *__restrict__ in,
+                                          const float *__restrict__ in2, const int64_t *stride,
+                                          const int *box_lo, const int *box_len, int r0, int r1,
+                                          const TileShape &t, bool stream, SlotFn slot_fn,
+                                          RowFn row_fn, QuadFn quad_fn) {
+    static_assert(QMAX % U == 0, "QMAX must be a multiple of U");
+    const int gl = threadIdx.x & (t.LPR - 1), grp = threadIdx.x / t.LPR;
+    const int L = box_len[D - 1];
+    bool ok[QMAX];
+    SD sd[QMAX];
+#pragma unroll
+    for (int i = 0; i < QMAX; ++i) {
+        const int e0 = 4 * (gl + i * t.LPR) - t.head;
+        ok[i] = i < t.QL && e0 < L && e0 + 4 > 0;
+        sd[i] = slot_fn(i, e0);
+    }
+    const int64_t step = 4 * int64_t(t.LPR);
+    RowIter<D> it;
+    it.init(box_len, r0 + grp, t.G);
+    for (int r = r0 + grp; r < r1; r += t.G) {
+        int coords[kMaxDim];
+        int64_t start = box_lo[D - 1];
+#pragma unroll
+        for (int j = 0; j < D - 1; ++j) {
+            coords[j] = box_lo[j] + it.c[j];
+            start += int64_t(coords[j]) * stride[j];
+        }
+        it.next();
+        S st;
+        row_fn(coords, st);
+        const int64_t a0 = start - t.head + 4 * gl;
+        const float *p = in + a0;
+        const float *p2 = TWO ? in2 + a0 : nullptr;
+#pragma unroll
+        for (int i0 = 0; i0 < QMAX; i0 += U) {
+            if (i0 < t.QL) {
+                float4 v[U], v2[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (ok[i0 + u]) {
+                        const float4 *q = reinterpret_cast<const float4 *>(p + (i0 + u) * step);
+                        v[u] = stream ? __ldcs(q) : __ldg(q);
+                        if (TWO) v2[u] = __ldcs(reinterpret_cast<const float4 *>(p2 + (i0 + u) * step));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (ok[i0 + u]) quad_fn(st, sd[i0 + u], i0 + u, v[u], v2[u], a0 + (i0 + u) * step);
+            }
+        }
+    }
+}
+
 // shared-memory access by 32-bit shared-window address
 __device__ __forceinline__ void red_shared_add(uint32_t addr, uint32_t v) {
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
@@ -476,7 +594,8 @@ cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float
                             unsigned char *ws, const float *d_clip, float *d_grad_lut,
                             float *d_grad_clip, cudaStream_t st);
 size_t bwd_partial_floats(const Geom &g, int chunks);
-size_t hist_smem_bytes(const Geom &g, int copies);
+size_t hist_smem_bytes(const Geom &g, int copies, int group);
+int64_t hist_items(const Geom &g, int group);
 size_t map_smem_bytes(const Geom &g);
 bool map_replicated(const Geom &g);
 

@@ -35,10 +35,12 @@ int64_t n_cells(const Geom &g) {
 }
 
 // Default launch shapes (the autotuner may replace them).
-//   histogram: R lane copies, as many as keep the copy summation (P * R
-//   words per CTA) small next to the CTA's voxels and the shared memory at
-//   most 80 KiB; cluster size C, a power of two up to 8, grown while the
-//   grid is short of four CTAs per SM and every CTA keeps enough voxels;
+//   histogram: G kernels per work item along the last dimension, so that an
+//   item's rows span at least 64 elements (256 bytes); R lane copies, as many
+//   as keep the CTA's shared memory within 100 KiB and the copy summation
+//   (G * P * R words) small next to the item's voxels; cluster size C, a power
+//   of two up to 8, grown while the grid is short of four CTAs per SM and
+//   every CTA keeps at least 8192 voxels;
 //   mapping: enough CTAs for several waves on the SMs, each covering at least
 //   four rows of its cell.
 Tuning default_tuning(const Geom &g) {
@@ -46,13 +48,19 @@ Tuning default_tuning(const Geom &g) {
     t.hist_threads = 256;
     t.map_threads = 256;
     const int sms = 152;
+    const Dim &dl = g.d[g.D - 1];
+    int G = std::min(dl.n, std::max(1, (64 + dl.b - 1) / dl.b));
+    const int64_t vitem = g.V * G;
     int R = 32;
-    while (R > 1 && (int64_t(g.P) * R > std::max<int64_t>(g.V / 2, g.P) ||
-                     hist_smem_bytes(g, R) > 80 * 1024))
+    while (R > 1 && (hist_smem_bytes(g, R, G) > 100 * 1024 ||
+                     int64_t(g.P) * R * G > std::max<int64_t>(vitem / 2, int64_t(g.P) * G)))
         R >>= 1;
+    while (G > 1 && hist_smem_bytes(g, R, G) > 100 * 1024) G >>= 1;
+    t.hist_group = G;
     t.hist_copies = R;
+    const int64_t items = hist_items(g, G);
     int C = 1;
-    while (C < 8 && g.K * C < 4 * sms && g.V / (2 * C) >= 2 * int64_t(g.P) * R) C <<= 1;
+    while (C < 8 && items * C < 4 * sms && vitem / (2 * C) >= 8192) C <<= 1;
     t.hist_chunks = C;
     int64_t rows = 1;   // rows of an interior cell
     for (int j = 0; j + 1 < g.D; ++j) rows *= g.d[j].b;
@@ -195,7 +203,7 @@ mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
     }
     // the 2^D neighbouring tables and one histogram (one lane copy at the
     // least) must fit in a CTA's shared memory
-    if (map_smem_bytes(g) > 200 * 1024 || hist_smem_bytes(g, 1) > 200 * 1024)
+    if (map_smem_bytes(g) > 200 * 1024 || hist_smem_bytes(g, 1, 1) > 200 * 1024)
         return MCLAHE_ERR_UNSUPPORTED;
     // CTAs per footprint row range: counts must stay in 32 bits
     int64_t foot = 1;
@@ -248,6 +256,12 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->ws_lut = p->ws.lut;
     info->ws_scratch = p->ws.scratch;
     info->ws_bytes = p->ws.total;
+    info->hist_group = p->t.hist_group;
+    info->hist_cluster = p->t.hist_chunks;
+    info->hist_copies = p->t.hist_copies;
+    info->map_chunks = p->t.map_chunks;
+    info->bwd_chunks = p->t.bwd_chunks;
+    info->tuned = p->tuned;
     return MCLAHE_OK;
 }
 

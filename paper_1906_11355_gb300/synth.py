@@ -172,3 +172,119 @@ def make_volume(gen, shape, seed):
     if gen == "photoemission":
         return photoemission(shape, seed=seed)
     raise ValueError(gen)
+
+
+# ---------------------------------------------------------------------------
+# The same recipes drawn with torch on a device (for large benchmark inputs).
+# They follow the numpy generators above step by step but use torch's random
+# streams (torch.Generator seeded with the same seed), so they give volumes of
+# the same distribution, not the same samples.
+# ---------------------------------------------------------------------------
+def _tgen(seed, device):
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def smooth_field_t(shape, seed=0, device="cuda", n_gauss=20, sigma=(20.0, 80.0), scale=0.6,
+                   noise_sd=0.02):
+    """smooth_field drawn on a device (float32 tensor)."""
+    import torch
+
+    g = _tgen(seed, device)
+    shape = tuple(int(s) for s in shape)
+    u = lambda lo, hi: float(torch.rand((), generator=g, device=device)) * (hi - lo) + lo
+    field = torch.zeros(shape, dtype=torch.float32, device=device)
+    for _ in range(n_gauss):
+        amp = u(0.0, 1.0)
+        sig = u(*sigma)
+        prod = None
+        for d, s in enumerate(shape):
+            c = u(0.0, s)
+            ax = torch.arange(s, dtype=torch.float32, device=device)
+            e = torch.exp(-((ax - c) ** 2) / (2.0 * sig * sig))
+            e = e.reshape([-1 if i == d else 1 for i in range(len(shape))])
+            prod = e if prod is None else prod * e
+        field += amp * prod
+    lo, hi = field.min(), field.max()
+    field = (field - lo) / (hi - lo).clamp_min(1e-30)
+    field = field * scale + noise_sd * torch.randn(shape, generator=g, device=device)
+    return field.clamp_(0.0, 1.0).contiguous()
+
+
+def _gauss_blur_t(vol, sigmas):
+    """Separable Gaussian blur (zero boundary), kernel radius 4 sigma."""
+    import torch
+    import torch.nn.functional as F
+
+    nd = vol.dim()
+    for d, sig in enumerate(sigmas):
+        if sig <= 0:
+            continue
+        r = max(1, int(4.0 * sig + 0.5))
+        x = torch.arange(-r, r + 1, dtype=torch.float32, device=vol.device)
+        k = torch.exp(-x * x / (2.0 * sig * sig))
+        k = (k / k.sum()).view(1, 1, -1)
+        v = vol.movedim(d, -1)
+        sh = v.shape
+        v = F.conv1d(v.reshape(-1, 1, sh[-1]), k, padding=r).reshape(sh)
+        vol = v.movedim(-1, d)
+    return vol.contiguous()
+
+
+def fluorescence_t(shape=(64, 512, 512), seed=1, device="cuda", n_emitters=None,
+                   psf_sigma=(3.0, 1.5, 1.5), atten=40.0, peak=4000.0, offset=100.0):
+    """fluorescence (normalised uint16 counts, float32) drawn on a device."""
+    import torch
+
+    g = _tgen(seed, device)
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    if n_emitters is None:
+        n_emitters = max(1, int(round(2000 * n / (64 * 512 * 512))))
+    vol = torch.zeros(n, dtype=torch.float32, device=device)
+    idx = torch.randint(0, n, (n_emitters,), generator=g, device=device)
+    br = 0.5 + 0.5 * torch.rand(n_emitters, generator=g, device=device)
+    vol.index_add_(0, idx, br)
+    vol = _gauss_blur_t(vol.view(shape), psf_sigma[-len(shape):])
+    vol = vol / vol.max().clamp_min(1e-30)
+    z = torch.arange(shape[0], dtype=torch.float32, device=device)
+    vol = vol * torch.exp(-z / atten).view([-1] + [1] * (len(shape) - 1))
+    lam = vol * peak + offset
+    counts = torch.poisson(lam, generator=g).clamp_(0, 65535)
+    return (counts / 65535.0).contiguous()
+
+
+def photoemission_t(shape=(128, 128, 256, 32), seed=2, device="cuda", n_bands=3, gamma=0.05,
+                    tau=10.0, e_fermi=0.6, kt=0.01, peak=50.0):
+    """photoemission drawn on a device (float32 Poisson counts)."""
+    import torch
+
+    g = _tgen(seed, device)
+    nkx, nky, ne, nt = (int(s) for s in shape)
+    kx = torch.linspace(-1.0, 1.0, nkx, device=device).view(-1, 1, 1)
+    ky = torch.linspace(-1.0, 1.0, nky, device=device).view(1, -1, 1)
+    e = torch.linspace(0.0, 1.0, ne, device=device).view(1, 1, -1)
+    a = (torch.rand(n_bands, generator=g, device=device) * 0.7 - 0.35).tolist()
+    c = (torch.rand(n_bands, generator=g, device=device) * 0.6 + 0.15).tolist()
+    spec = torch.zeros((nkx, nky, ne), dtype=torch.float32, device=device)
+    for i in range(n_bands):
+        eb = a[i] * (kx * kx + ky * ky) + c[i]
+        spec += gamma * gamma / ((e - eb) ** 2 + gamma * gamma)
+    spec *= 1.0 / (1.0 + torch.exp((e - e_fermi) / kt))
+    spec *= peak / spec.max()
+    decay = torch.exp(-torch.arange(nt, dtype=torch.float32, device=device) / tau)
+    lam = spec.unsqueeze(-1) * decay
+    return torch.poisson(lam, generator=g).contiguous()
+
+
+def batch_volume_t(spec, device="cuda"):
+    """batch_volume drawn on a device."""
+    nd = len(spec["shape"])
+    if nd == 2:
+        return smooth_field_t(spec["shape"], seed=spec["seed"], device=device)
+    if nd == 3:
+        return fluorescence_t(spec["shape"], seed=spec["seed"], device=device)
+    return photoemission_t(spec["shape"], seed=spec["seed"], device=device)

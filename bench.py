@@ -57,8 +57,9 @@ def parse():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
-            int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_1906_11355_gb300.dist import dist_env as env
+
+    return env()
 
 
 def measured_peak_gbs():
@@ -403,7 +404,9 @@ def run_native(args):
     nbuild.build()
     nat.load()
     w = synth.WORKLOADS[args.workload]
-    x_host = synth.make_volume(w["gen"], w["shape"], w["seed"] + 7919 * rank)
+    from paper_1906_11355_gb300.dist import max_over_ranks, rank_seed
+
+    x_host = synth.make_volume(w["gen"], w["shape"], rank_seed(w["seed"], rank))
     op = MCLAHE(w["shape"], w["kernel"], w["n_bins"], float(np.float32(w["clip_limit"])),
                 adaptive=w["adaptive"], device=dev)
     x = torch.from_numpy(x_host).to(dev)
@@ -450,10 +453,7 @@ def run_native(args):
     pass_ms = {nat.PASS_NAMES[p]: sum(ev[p].elapsed_time(ev[p + 1]) for ev in events) / args.steps
                for p in passes}
     ms = sum(step_ms) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device=dev)   # the slowest rank sets the whole-job time
     voxels = int(np.prod(w["shape"]))
     value = voxels * world / (ms * 1e-3) / 1e9
 

@@ -555,15 +555,10 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                     uint32_t base;   // copy address of bin 0 minus the bias; ~0: per-voxel path
                     uint32_t w;      // weight of the slot's voxels
                     int q0;          // element offset of the slot in the row
-                    float2 nl, sc;   // the kernel's quantiser constants (adaptive range)
+                    int kg;          // the slot's kernel (adaptive range constants)
                 };
                 auto slot = [&](int, int e0) {
-                    HSlot sd;
-                    sd.base = 0xffffffffu;
-                    sd.w = 0;
-                    sd.q0 = e0;
-                    sd.nl = make_float2(0.f, 0.f);
-                    sd.sc = sd.nl;
+                    HSlot sd{0xffffffffu, 0u, e0, 0};
                     if (e0 < 0 || e0 + 4 > L) return sd;
                     int kg0[3], m0[3], kg1[3], m1[3];
                     if (last_targets(dl, xs + e0, kl0, kl1, kg0, m0) != 1 ||
@@ -572,16 +567,17 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                         return sd;
                     sd.base = sh_base + uint32_t(kg0[0]) * kstride + lane_off - kBinBias * r4;
                     sd.w = wu * uint32_t(m0[0]);
-                    if (ADAPTIVE) {
-                        sd.nl = make_float2(s_nlo[kg0[0]], s_nlo[kg0[0]]);
-                        sd.sc = make_float2(s_sc[kg0[0]], s_sc[kg0[0]]);
-                    }
+                    sd.kg = kg0[0];
                     return sd;
                 };
                 const float2 gnl = make_float2(s_nlo[0], s_nlo[0]), gsc = make_float2(s_sc[0], s_sc[0]);
                 auto quad = [&](NoRow &, const HSlot &sd, int, const float4 &v, const float4 &, int64_t) {
                     if (sd.base != 0xffffffffu) {
-                        const float2 n2 = ADAPTIVE ? sd.nl : gnl, s2 = ADAPTIVE ? sd.sc : gsc;
+                        float2 n2 = gnl, s2 = gsc;
+                        if (ADAPTIVE) {
+                            n2 = make_float2(s_nlo[sd.kg], s_nlo[sd.kg]);
+                            s2 = make_float2(s_sc[sd.kg], s_sc[sd.kg]);
+                        }
                         const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
                         const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
                         red_shared_add(b01.x * r4 + sd.base, sd.w);

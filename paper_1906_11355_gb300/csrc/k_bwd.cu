@@ -9,8 +9,9 @@
 // Three launches:
 //   k_adj     one CTA per chunk of an inter-kernel cell: streams the input and
 //             the upstream gradient, accumulates g * c_i into the cell's 2^D
-//             corner tables in shared memory (float reductions) and writes
-//             them as the chunk's partial table gradients;
+//             corner tables in shared memory (float reductions, lane-rotated
+//             copies: conflict-free whatever the bins) and writes them, copies
+//             summed, as the chunk's partial table gradients;
 //   k_lutbwd  one CTA per kernel: sums the partials of the cells around the
 //             kernel in a fixed order (deterministic), folds the padded table
 //             indices, stores dL/dlut, and takes the reverse of clip,
@@ -23,20 +24,33 @@
 //             the clip limit given lies outside [0, 1], where the forward
 //             clamps it).
 #include "hist_impl.cuh"
+#include "map_impl.cuh"   // rotate_left
 
 namespace mclahe {
 
-template <int D, bool ADAPTIVE>
-__global__ void __launch_bounds__(256) k_adj(Geom g, const float *__restrict__ in,
-                                             const float *__restrict__ gout,
-                                             const float *__restrict__ lo_k,
-                                             const float *__restrict__ scale_k,
-                                             float *__restrict__ part, int chunks) {
+// Accumulator layout of k_adj.  REPL: [corner][index][copy] with 32 / 2^D
+// copies; lane l adds, at step t, to corner (t + l) mod 2^D in copy l / 2^D,
+// so the 32 lanes of a warp always touch 32 different words in 32 different
+// banks (the index is shared or not); the lane rotation is undone by rotated
+// per-lane weights and ranges, as in the mapping pass.  Plain: [corner][index].
+__host__ __device__ inline bool adj_repl(int P) { return size_t(P) * 128 <= 160 * 1024; }
+__host__ __device__ inline size_t adj_smem(int D, int P) {
+    return adj_repl(P) ? size_t(P) * 128 : (size_t(1) << D) * size_t(P) * sizeof(float);
+}
+
+template <int D, bool ADAPTIVE, bool REPL>
+__global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict__ in,
+                                                const float *__restrict__ gout,
+                                                const float *__restrict__ lo_k,
+                                                const float *__restrict__ scale_k,
+                                                float *__restrict__ part, int chunks) {
     constexpr int NC = 1 << D;
     constexpr int NO = 1 << (D - 1);
-    extern __shared__ __align__(16) float acc[];   // NC x P, corner-major
+    constexpr int RC = REPL ? 32 / NC : 1;      // copies
+    extern __shared__ __align__(16) float acc[];
     __shared__ float s_nlo[NC], s_sc[NC];
     const int P = g.P, LS = g.LS;
+    const int lane = threadIdx.x & 31;
     const int64_t cell = blockIdx.x / chunks;
     const int chunk = int(blockIdx.x - cell * chunks);
 
@@ -59,13 +73,18 @@ __global__ void __launch_bounds__(256) k_adj(Geom g, const float *__restrict__ i
             st *= g.d[d].n;
         }
     }
-    for (int i = threadIdx.x; i < NC * P; i += blockDim.x) acc[i] = 0.0f;
+    {
+        float4 *z = reinterpret_cast<float4 *>(acc);
+        const int n4 = int(NC * P * RC / 4);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = n4 * 4 + threadIdx.x; i < NC * P * RC; i += blockDim.x) acc[i] = 0.0f;
+    }
     if (threadIdx.x < NC) {
         int64_t k = kbase;
 #pragma unroll
         for (int d = 0; d < D; ++d) k += ((threadIdx.x >> (D - 1 - d)) & 1) ? kstr[d] : 0;
-        s_nlo[threadIdx.x] = -lo_k[k];
-        s_sc[threadIdx.x] = scale_k[k];
+        s_nlo[threadIdx.x] = -__ldcg(lo_k + k);
+        s_sc[threadIdx.x] = __ldcg(scale_k + k);
     }
     int box_lo[kMaxDim], len[kMaxDim];
     int64_t stride[kMaxDim];
@@ -94,63 +113,107 @@ __global__ void __launch_bounds__(256) k_adj(Geom g, const float *__restrict__ i
     }
     const uint32_t acc_s = uint32_t(__cvta_generic_to_shared(acc));
     const float iqk = g.iqk, qkf = g.qkf;
+    const int rot = REPL ? (lane & (NC - 1)) : 0;
+    const int copy = REPL ? (lane / NC) : 0;
+    constexpr uint32_t IB = uint32_t(4 * RC);   // bytes per table index
+    // per step t: corner (t + rot) mod NC, its range and accumulator base
     float nl[NC], sc[NC];
     uint32_t cbase[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        nl[c] = s_nlo[c];
-        sc[c] = s_sc[c];
-        cbase[c] = acc_s + 4u * uint32_t(c * P) - kBinBias * 4u;
+    for (int t = 0; t < NC; ++t) {
+        const int c = (t + rot) & (NC - 1);
+        nl[t] = s_nlo[c];
+        sc[t] = s_sc[c];
+        cbase[t] = acc_s + uint32_t(c * P) * IB + 4u * uint32_t(copy) - kBinBias * IB;
     }
     const int L = len[D - 1];
     const int xl = box_lo[D - 1];
-    const bool same_align = (D == 1) || ((g.d[D >= 2 ? D - 2 : 0].stride & 3) == 0);
     const float inv2b_l = inv2b[D - 1];
+    const float two_inv2b = 2.0f * inv2b_l;
     const int mb_l = mb[D - 1];
+    const int rodd = rot & 1;
 
+    // per row: the outer weight of the corner each step handles
     struct BRow {
-        float wo[NO];
+        float w[NC];
     };
-    auto row_fn = [&](const int *coords, int64_t, BRow &st) {
+    auto row_fn = [&](const int *coords, BRow &st) {
+        float wo[NO];
 #pragma unroll
-        for (int i = 0; i < NO; ++i) st.wo[i] = 1.0f;
+        for (int i = 0; i < NO; ++i) wo[i] = 1.0f;
 #pragma unroll
         for (int j = 0; j < D - 1; ++j) {
             const float w1 = float(2 * coords[j] + mb[j]) * inv2b[j];
             const float w0 = 1.0f - w1;
 #pragma unroll
-            for (int i = 0; i < NO; ++i) st.wo[i] *= ((i >> (D - 2 - j)) & 1) ? w1 : w0;
+            for (int i = 0; i < NO; ++i) wo[i] *= ((i >> (D - 2 - j)) & 1) ? w1 : w0;
+        }
+        float a[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) a[c] = wo[c >> 1];
+        if (REPL) rotate_left<NC>(a, rot);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) st.w[c] = a[c];
+    };
+    // adds g * c_i for the voxel (x, g) at last-dim weight w1
+    auto add = [&](const BRow &st, float x, float gv, float w1) {
+        const float gw1 = gv * w1, gw0 = gv - gw1;
+        const float ge = rodd ? gw1 : gw0, go = rodd ? gw0 : gw1;   // even / odd steps
+        const uint32_t gbits = ADAPTIVE ? 0u : qbits1(x, nl[0], sc[0], iqk, qkf);
+#pragma unroll
+        for (int t = 0; t < NC; ++t) {
+            const uint32_t b = ADAPTIVE ? qbits1(x, nl[t], sc[t], iqk, qkf) : gbits;
+            const float v = st.w[t] * ((t & 1) ? go : ge);
+            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(b * IB + cbase[t]), "f"(v) : "memory");
         }
     };
-    auto quad_fn = [&](BRow &st, const QuadRef &q) {
-        if (!q.has) return;
-        const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
-        const float gs[4] = {q.v2.x, q.v2.y, q.v2.z, q.v2.w};
-        const float fb = float(2 * (xl + q.e0) + mb_l);
+    if ((g.d[D - 1].s & 3) == 0) {
+        struct BSlot {
+            float fbi;   // last-dim weight w1 of the slot's first voxel
+            int e0;
+        };
+        const TileShape ts = tile_shape(L, xl & 3, blockDim.x, 4);
+        auto slot = [&](int, int e0) {
+            BSlot sd;
+            sd.e0 = e0;
+            sd.fbi = float(2 * (xl + e0) + mb_l) * inv2b_l;
+            return sd;
+        };
+        auto quad = [&](BRow &st, const BSlot &sd, int, const float4 &v, const float4 &gq, int64_t) {
+            const float vals[4] = {v.x, v.y, v.z, v.w};
+            const float gs[4] = {gq.x, gq.y, gq.z, gq.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int el = q.e0 + e;
-            if (el < 0 || el >= L) continue;
-            const float w1 = (fb + float(2 * e)) * inv2b_l;
-            const float w0 = 1.0f - w1;
-            const float gw0 = gs[e] * w0, gw1 = gs[e] * w1;
-            const uint32_t gbits = ADAPTIVE ? 0u : qbits1(vals[e], nl[0], sc[0], iqk, qkf);
+            for (int e = 0; e < 4; ++e)
+                if (sd.e0 + e >= 0 && sd.e0 + e < L) add(st, vals[e], gs[e], fmaf(float(e), two_inv2b, sd.fbi));
+        };
+        walk_tile<D, 4, 2, BRow, BSlot, true>(in, gout, stride, box_lo, len, r0, r1, ts, true, slot,
+                                              row_fn, quad);
+    } else {
+        auto row64 = [&](const int *coords, int64_t, BRow &st) { row_fn(coords, st); };
+        auto quad_fn = [&](BRow &st, const QuadRef &q) {
+            if (!q.has) return;
+            const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+            const float gs[4] = {q.v2.x, q.v2.y, q.v2.z, q.v2.w};
+            const float fbi = float(2 * (xl + q.e0) + mb_l) * inv2b_l;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const uint32_t b = ADAPTIVE ? qbits1(vals[e], nl[c], sc[c], iqk, qkf) : gbits;
-                const float v = st.wo[c >> 1] * ((c & 1) ? gw1 : gw0);
-                asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(b * 4u + cbase[c]), "f"(v)
-                             : "memory");
-            }
-        }
-    };
-    walk_box<D, 4, BRow, true>(in, gout, g.N, stride, box_lo, len, r0, r1, same_align, true,
-                               row_fn, quad_fn);
+            for (int e = 0; e < 4; ++e)
+                if (q.e0 + e >= 0 && q.e0 + e < L) add(st, vals[e], gs[e], fmaf(float(e), two_inv2b, fbi));
+        };
+        walk_box<D, 4, BRow, true>(in, gout, g.N, stride, box_lo, len, r0, r1, false, true, row64,
+                                   quad_fn);
+    }
     __syncthreads();
+    // the chunk's partial table gradients, copies summed
     float *dst = part + (cell * chunks + chunk) * NC * LS;
     for (int i = threadIdx.x; i < NC * LS; i += blockDim.x) {
         const int c = i / LS, j = i - c * LS;
-        dst[i] = j < P ? acc[c * P + j] : 0.0f;
+        float v = 0.0f;
+        if (j < P) {
+            const float *a = acc + (size_t(c) * P + j) * RC;
+#pragma unroll
+            for (int q = 0; q < RC; ++q) v += a[q];
+        }
+        dst[i] = v;
     }
 }
 
@@ -264,20 +327,23 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
     const int chunks = p.t.bwd_chunks;
     float *part = reinterpret_cast<float *>(ws + p.ws.scratch);
     float *dT = part + bwd_partial_floats(g, chunks);
-    const size_t smem_adj = (size_t(1) << D) * g.P * sizeof(float);
+    const size_t smem_adj = adj_smem(D, g.P);
     const unsigned grid = unsigned(n_cells(g) * chunks);
+    const bool repl = adj_repl(g.P);
+    const float *lo = reinterpret_cast<const float *>(ws + p.ws.lo);
+    const float *sc = reinterpret_cast<const float *>(ws + p.ws.scale);
     cudaError_t e;
+#define MCLAHE_ADJ(A, R)                                                                       \
+    e = cudaFuncSetAttribute(k_adj<D, A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                             int(smem_adj));                                                   \
+    if (e != cudaSuccess) return e;                                                            \
+    k_adj<D, A, R><<<grid, 256, smem_adj, st>>>(g, in, gout, lo, sc, part, chunks);
     if (g.mode == MCLAHE_RANGE_ADAPTIVE) {
-        e = cudaFuncSetAttribute(k_adj<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_adj));
-        if (e != cudaSuccess) return e;
-        k_adj<D, true><<<grid, 256, smem_adj, st>>>(g, in, gout, reinterpret_cast<const float *>(ws + p.ws.lo),
-                                                    reinterpret_cast<const float *>(ws + p.ws.scale), part, chunks);
+        if (repl) { MCLAHE_ADJ(true, true) } else { MCLAHE_ADJ(true, false) }
     } else {
-        e = cudaFuncSetAttribute(k_adj<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_adj));
-        if (e != cudaSuccess) return e;
-        k_adj<D, false><<<grid, 256, smem_adj, st>>>(g, in, gout, reinterpret_cast<const float *>(ws + p.ws.lo),
-                                                     reinterpret_cast<const float *>(ws + p.ws.scale), part, chunks);
+        if (repl) { MCLAHE_ADJ(false, true) } else { MCLAHE_ADJ(false, false) }
     }
+#undef MCLAHE_ADJ
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem_lb = size_t(g.P) * sizeof(float) + size_t(g.nb) * sizeof(uint32_t);
     e = cudaFuncSetAttribute(k_lutbwd<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_lb));

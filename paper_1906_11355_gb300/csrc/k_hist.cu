@@ -7,7 +7,7 @@
 namespace mclahe {
 
 template <int D, bool ADAPTIVE>
-__global__ void __launch_bounds__(256, 3) k_hist(Geom g, const float *__restrict__ in,
+__global__ void __launch_bounds__(256, D >= 4 ? 2 : 3) k_hist(Geom g, const float *__restrict__ in,
                                               const uint32_t *__restrict__ keys,
                                               const float *__restrict__ d_clip,
                                               uint32_t *__restrict__ hist, float *__restrict__ lut,

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256, D <= 2 ? 3 : ((D >= 4 && ADAPTIVE) ? 1 : 
                 wait_ready(&bp.done[2 * vi + 1], uint32_t(V.n_hist), bp.status);
                 const int64_t cell = idx / V.mgroups;
                 const int grp = int(idx - cell * V.mgroups);
-                map_cell<D, ADAPTIVE, true>(V.g, V.in, V.out, V.lut, V.lo, V.scale, cell,
+                map_cell<D, ADAPTIVE, true, false>(V.g, V.in, V.out, V.lut, V.lo, V.scale, cell,
                                             grp * C + rank, V.mgroups * C,
                                             reinterpret_cast<float *>(smem));
                 break;

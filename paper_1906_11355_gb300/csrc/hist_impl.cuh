@@ -236,26 +236,47 @@ __host__ __device__ inline size_t hist_smem_words(int P, int R, int G) {
 // Kernels (relative to kl0, among [kl0, kl1)) that hold an image of the
 // original index x along one dimension, with multiplicities (Sec. III.B: x
 // has its main image at x + p0 and mirror images at p0 - 1 - x for x < p0 and
-// at 2s - 1 - x + p0 for x >= s - p1).  Returns the number of distinct kernels.
-__device__ __forceinline__ int last_targets(const Dim &d, int x, int kl0, int kl1, int *kg, int *m) {
-    int P[3], np = 0;
-    P[np++] = x + d.p0;
-    if (x < d.p0) P[np++] = d.p0 - 1 - x;
-    if (x >= d.s - d.p1) P[np++] = 2 * d.s - 1 - x + d.p0;
-    int n = 0;
-    for (int i = 0; i < np; ++i) {
-        const int k = P[i] / d.b;
-        if (k < kl0 || k >= kl1) continue;
-        int j = 0;
-        while (j < n && kg[j] != k - kl0) ++j;
-        if (j == n) {
-            kg[n] = k - kl0;
-            m[n] = 0;
-            ++n;
-        }
-        m[j] += 1;
+// at 2s - 1 - x + p0 for x >= s - p1).
+struct Targets {
+    int n;               // distinct kernels
+    int kg[3], m[3];     // group-relative kernel and multiplicity (static indices only)
+};
+
+__device__ __forceinline__ Targets last_targets(const Dim &d, int x, int kl0, int kl1) {
+    int kc[3];
+    kc[0] = (x + d.p0) / d.b;
+    kc[1] = (x < d.p0) ? (d.p0 - 1 - x) / d.b : -1;
+    kc[2] = (x >= d.s - d.p1) ? (2 * d.s - 1 - x + d.p0) / d.b : -1;
+    Targets t;
+    t.n = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        t.kg[i] = 0;
+        t.m[i] = 0;
     }
-    return n;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int k = kc[i];
+        if (k < kl0 || k >= kl1) continue;
+        bool merged = false;
+#pragma unroll
+        for (int j = 0; j < i; ++j)
+            if (j < t.n && t.kg[j] == k - kl0) {
+                t.m[j] += 1;
+                merged = true;
+            }
+        if (!merged) {
+            // append at position t.n (0..2) with static stores
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (j == t.n) {
+                    t.kg[j] = k - kl0;
+                    t.m[j] = 1;
+                }
+            t.n += 1;
+        }
+    }
+    return t;
 }
 
 constexpr int kHistQmax = 4;   // quad slots per thread and row in the histogram pass
@@ -304,14 +325,15 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         for (int i = (nw / 4) * 4 + threadIdx.x; i < nw; i += blockDim.x) sh[i] = 0;
     }
 
-    // outer pieces (dims 0..D-2) and the last-dim extent of the group
-    Pieces pc[kMaxDim];
+    // outer pieces (dims 0..D-2) and the last-dim extent of the group, in
+    // shared memory (the same for every thread)
+    __shared__ Pieces pc[kMaxDim + 1];
+    if (threadIdx.x < D - 1) pc[threadIdx.x] = footprint_pieces(g.d[threadIdx.x], kk[threadIdx.x]);
+    if (threadIdx.x == kMaxDim) pc[kMaxDim] = footprint_pieces(dl, kl0);   // one-kernel groups
+    __syncthreads();
     int nsub = 1;
 #pragma unroll
-    for (int j = 0; j < D - 1; ++j) {
-        pc[j] = footprint_pieces(g.d[j], kk[j]);
-        nsub *= pc[j].n;
-    }
+    for (int j = 0; j < D - 1; ++j) nsub *= pc[j].n;
     int xlo = dl.s, xhi = 0;
     for (int k = kl0; k < kl1; ++k) {
         const Foot f = footprint(dl, k);
@@ -329,9 +351,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     // kernel kgfix = 0; otherwise kgfix = -1 and the boxes are segments of
     // the group's extent whose voxels are assigned to kernels quad by quad.
     const bool single = GK == 1;
-    Pieces pl;
-    pl.n = 0;
-    if (single) pl = footprint_pieces(dl, kl0);
+    const Pieces &pl = pc[kMaxDim];
     auto for_boxes = [&](auto &&fn) {
         for (int sb = 0; sb < nsub; ++sb) {
             int box_lo[kMaxDim], len[kMaxDim];
@@ -390,12 +410,13 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         auto key_min = [&](int kg, float v) { atomicMax(&s_keys[2 * kg], ~float_key(v)); };
         auto key_max = [&](int kg, float v) { atomicMax(&s_keys[2 * kg + 1], float_key(v)); };
         auto slow_elem = [&](int x, float v) {
-            int kg[3], m[3];
-            const int n = last_targets(dl, x, kl0, kl1, kg, m);
-            for (int t = 0; t < n; ++t) {
-                key_min(kg[t], v);
-                key_max(kg[t], v);
-            }
+            const Targets tg = last_targets(dl, x, kl0, kl1);
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t < tg.n) {
+                    key_min(tg.kg[t], v);
+                    key_max(tg.kg[t], v);
+                }
         };
         for_boxes([&](const int *box_lo, const int *len, int, int r0, int r1, int kgfix) {
             const int L = len[D - 1], xs = box_lo[D - 1];
@@ -421,10 +442,9 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                     } else if (sd.full) {
                         // the targets change monotonically along x, so equal
                         // single targets at both ends hold for the whole quad
-                        int kg0[3], m0[3], kg1[3], m1[3];
-                        if (last_targets(dl, xs + e0, kl0, kl1, kg0, m0) == 1 &&
-                            last_targets(dl, xs + e0 + 3, kl0, kl1, kg1, m1) == 1 && kg1[0] == kg0[0])
-                            sd.kg = kg0[0];
+                        const Targets t0 = last_targets(dl, xs + e0, kl0, kl1);
+                        const Targets t1 = last_targets(dl, xs + e0 + 3, kl0, kl1);
+                        if (t0.n == 1 && t1.n == 1 && t1.kg[0] == t0.kg[0]) sd.kg = t0.kg[0];
                     }
                     tk[i] = sd.full ? sd.kg : -1;
                     return sd;
@@ -507,13 +527,15 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         const uint32_t kstride = uint32_t(P) * r4;   // bytes per kernel's copies
         const float iqk = g.iqk, qkf = g.qkf;
         auto add_elem = [&](int x, float v, uint32_t w) {
-            int kg[3], m[3];
-            const int n = last_targets(dl, x, kl0, kl1, kg, m);
-            for (int t = 0; t < n; ++t) {
-                const uint32_t b = qbits1(v, s_nlo[kg[t]], s_sc[kg[t]], iqk, qkf);
-                red_shared_add(sh_base + uint32_t(kg[t]) * kstride + lane_off + (b - kBinBias) * r4,
-                               w * uint32_t(m[t]));
-            }
+            const Targets tg = last_targets(dl, x, kl0, kl1);
+#pragma unroll
+            for (int t = 0; t < 3; ++t)
+                if (t < tg.n) {
+                    const int kg = tg.kg[t];
+                    const uint32_t b = qbits1(v, s_nlo[kg], s_sc[kg], iqk, qkf);
+                    red_shared_add(sh_base + uint32_t(kg) * kstride + lane_off + (b - kBinBias) * r4,
+                                   w * uint32_t(tg.m[t]));
+                }
         };
         for_boxes([&](const int *box_lo, const int *len, int w, int r0, int r1, int kgfix) {
             const int L = len[D - 1], xs = box_lo[D - 1];
@@ -560,14 +582,12 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                 auto slot = [&](int, int e0) {
                     HSlot sd{0xffffffffu, 0u, e0, 0};
                     if (e0 < 0 || e0 + 4 > L) return sd;
-                    int kg0[3], m0[3], kg1[3], m1[3];
-                    if (last_targets(dl, xs + e0, kl0, kl1, kg0, m0) != 1 ||
-                        last_targets(dl, xs + e0 + 3, kl0, kl1, kg1, m1) != 1 || kg1[0] != kg0[0] ||
-                        m1[0] != m0[0])
-                        return sd;
-                    sd.base = sh_base + uint32_t(kg0[0]) * kstride + lane_off - kBinBias * r4;
-                    sd.w = wu * uint32_t(m0[0]);
-                    sd.kg = kg0[0];
+                    const Targets t0 = last_targets(dl, xs + e0, kl0, kl1);
+                    const Targets t1 = last_targets(dl, xs + e0 + 3, kl0, kl1);
+                    if (t0.n != 1 || t1.n != 1 || t1.kg[0] != t0.kg[0] || t1.m[0] != t0.m[0]) return sd;
+                    sd.base = sh_base + uint32_t(t0.kg[0]) * kstride + lane_off - kBinBias * r4;
+                    sd.w = wu * uint32_t(t0.m[0]);
+                    sd.kg = t0.kg[0];
                     return sd;
                 };
                 const float2 gnl = make_float2(s_nlo[0], s_nlo[0]), gsc = make_float2(s_sc[0], s_sc[0]);

@@ -31,6 +31,10 @@
 // order is undone by per-lane rotated copies of the corner ranges and
 // weights, built once per CTA and per row.  Tables too large for this layout
 // (more than 1280 entries) use one row of 2^D values per index.
+//
+// Every table has lut[.][0] = 0 (the normalisation subtracts the first CDF
+// value), so with a global range a voxel in bin 0 maps to exactly 0 and its
+// gathers are skipped (count data are mostly zeros).
 #pragma once
 
 #include "mclahe_internal.cuh"
@@ -54,13 +58,22 @@ __device__ __forceinline__ void rotate_left(T (&a)[N], int r) {
 
 // The replicated layout needs 128 bytes per table index.
 __host__ __device__ inline bool map_repl_fits(int P) { return size_t(P) * 128 <= 160 * 1024; }
-__host__ __device__ inline size_t map_smem_for(int D, int P) {
+__host__ __device__ inline size_t map_table_bytes(int D, int P) {
     return map_repl_fits(P) ? size_t(P) * 128 : (size_t(1) << D) * size_t(P) * sizeof(float);
+}
+// Rows of 3- and 4-D cells stream through a cp.async ring (walk_tile_async):
+// kMapStages row stages of up to 4 quads per thread of a 256-thread CTA.
+constexpr int kMapStages = 3;
+__host__ __device__ inline size_t map_ring_bytes(int D) {
+    return D >= 3 ? size_t(kMapStages) * 4 * 256 * 16 : 0;
+}
+__host__ __device__ inline size_t map_smem_for(int D, int P, bool ring = true) {
+    return ((map_table_bytes(D, P) + 15) & ~size_t(15)) + (ring ? map_ring_bytes(D) : 0);
 }
 
 __device__ __forceinline__ void sts128(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-template <int D, bool ADAPTIVE, bool REPL>
+template <int D, bool ADAPTIVE, bool REPL, bool RING = true>
 __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict__ in,
                                          float *__restrict__ out, const float *__restrict__ lut,
                                          const float *__restrict__ lo_k,
@@ -105,11 +118,16 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     if (REPL) {
         if (NC >= 4) {
             // task (j, q): corners 4q..4q+3 of index j into every copy's quad q
+            // AHR: slot s holds corner s mod NC.  GHR: quad q holds the corners
+            // (outer 2q, side 0), (outer 2q + 1, side 0), (2q, side 1),
+            // (2q + 1, side 1), so that one packed FMA takes the two outer
+            // corners' weights at once.
+            constexpr int P1 = ADAPTIVE ? 2 : 1, P2 = ADAPTIVE ? 1 : 2;
             for (int t = threadIdx.x; t < P * NQ; t += blockDim.x) {
                 const int j = t / NQ, q = t - j * NQ;
                 const float4 v = make_float4(__ldcg(lut + corner_kernel(4 * q) * LS + j),
-                                             __ldcg(lut + corner_kernel(4 * q + 1) * LS + j),
-                                             __ldcg(lut + corner_kernel(4 * q + 2) * LS + j),
+                                             __ldcg(lut + corner_kernel(4 * q + P2) * LS + j),
+                                             __ldcg(lut + corner_kernel(4 * q + P1) * LS + j),
                                              __ldcg(lut + corner_kernel(4 * q + 3) * LS + j));
 #pragma unroll
                 for (int a = 0; a < 8 / NQ; ++a) sts128(tab + j * 32 + (a * NQ + q) * 4, v);
@@ -125,7 +143,9 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     } else {
         for (int t = threadIdx.x; t < NC * P; t += blockDim.x) {
             const int j = t / NC, i = t - j * NC;
-            tab[t] = __ldcg(lut + corner_kernel(i) * LS + j);
+            // GHR quads hold (2q, 0), (2q + 1, 0), (2q, 1), (2q + 1, 1), as above
+            const int c = (ADAPTIVE || NC < 4) ? i : ((i & ~3) | ((i & 1) << 1) | ((i >> 1) & 1));
+            tab[t] = __ldcg(lut + corner_kernel(c) * LS + j);
         }
     }
     if (threadIdx.x < NC) {
@@ -218,7 +238,7 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     //   GHR: (wa[s], wb[s]) = outer weights of the two outer corners of quad
     //        (s + rot) mod NQ (corners 4q..4q+3 = outer 2q, 2q+1 x last 0, 1).
     struct MRow {
-        float2 w[ADAPTIVE ? NC / 2 : 2 * NQ];
+        float2 w[ADAPTIVE ? NC / 2 : (NC >= 4 ? NQ : 2)];
     };
     auto row_fn = [&](const int *coords, int64_t, MRow &st) {
         float wo[NO];
@@ -239,21 +259,13 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
 #pragma unroll
             for (int t = 0; t < NA / 2; ++t) st.w[t] = make_float2(a[2 * t], a[2 * t + 1]);
         } else if (NC >= 4) {
-            float pa[NQ], pb[NQ];
+            // (outer 2q, outer 2q + 1) weight pairs of the quads, in this lane's order
+            float2 pw[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                pa[q] = wo[2 * q];
-                pb[q] = wo[2 * q + 1];
-            }
-            if (REPL && NQ > 1) {
-                rotate_left<NQ>(pa, rot);
-                rotate_left<NQ>(pb, rot);
-            }
+            for (int q = 0; q < NQ; ++q) pw[q] = make_float2(wo[2 * q], wo[2 * q + 1]);
+            if (REPL && NQ > 1) rotate_left<NQ>(pw, rot);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                st.w[2 * q] = make_float2(pa[q], pa[q]);
-                st.w[2 * q + 1] = make_float2(pb[q], pb[q]);
-            }
+            for (int q = 0; q < NQ; ++q) st.w[q] = pw[q];
         } else {
             st.w[0] = make_float2(1.0f, 1.0f);
             st.w[1] = st.w[0];
@@ -292,16 +304,20 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                 // even steps read last-dim side rot & 1, odd steps the other
                 a0 = rodd ? acc.y : acc.x;
                 a1 = rodd ? acc.x : acc.y;
+            } else if (gb[e] == kBinBias) {
+                // bin 0: every table's first entry is 0, so the voxel maps to 0
+                a0 = 0.0f;
+                a1 = 0.0f;
             } else if (NC >= 4) {
-                float2 acc = make_float2(0.0f, 0.0f);
+                float2 acc0 = make_float2(0.0f, 0.0f), acc1 = acc0;   // sides 0 and 1
 #pragma unroll
                 for (int s = 0; s < NQ; ++s) {
                     const float4 t4 = lds_f32x4(gb[e] * RSB + gbase[s]);
-                    acc = __ffma2_rn(make_float2(t4.x, t4.y), st.w[2 * s], acc);
-                    acc = __ffma2_rn(make_float2(t4.z, t4.w), st.w[2 * s + 1], acc);
+                    acc0 = __ffma2_rn(make_float2(t4.x, t4.y), st.w[s], acc0);
+                    acc1 = __ffma2_rn(make_float2(t4.z, t4.w), st.w[s], acc1);
                 }
-                a0 = acc.x;
-                a1 = acc.y;
+                a0 = acc0.x + acc0.y;
+                a1 = acc1.x + acc1.y;
             } else {
                 const float2 t2 = lds_f32x2(gb[e] * RSB + gbase[0]);
                 a0 = t2.x;
@@ -341,8 +357,16 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             map4(st, vals, sd.fbi, res);
             store4(a, sd.e0, res);
         };
-        walk_tile<D, QM, (ADAPTIVE && D >= 3) ? 2 : 4, MRow, MSlot, false>(
-            in, nullptr, stride, box_lo, len, r0, r1, ts, true, slot, row2, quad);
+        if (RING && D >= 3) {
+            // rows stream through the cp.async ring behind the tables
+            float4 *ring = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(tab) +
+                                                      ((map_table_bytes(D, P) + 15) & ~size_t(15)));
+            walk_tile_async<D, QM, kMapStages, MRow, MSlot>(in, stride, box_lo, len, r0, r1, ts, ring,
+                                                             slot, row2, quad);
+        } else {
+            walk_tile<D, QM, 4, MRow, MSlot, false>(in, nullptr, stride, box_lo, len, r0, r1, ts, true,
+                                                    slot, row2, quad);
+        }
     } else {
         auto quad_fn = [&](MRow &st, const QuadRef &q) {
             if (!q.has) return;

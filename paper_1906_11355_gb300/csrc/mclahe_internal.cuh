@@ -481,7 +481,9 @@ __device__ __forceinline__ void walk_box(const float *__restrict__ in,
 // slot's data SD, row_fn(coords, state) runs once per row, and
 // quad_fn(state, slot data, i, v, v2, a) once per loaded quad (a = element
 // address of the quad's first element).  Loads are issued
-// U at a time; every loop is unrolled, so slot data stay in registers.  QL <= QMAX is required: boxes with rows longer
+// U at a time; every loop is unrolled, so slot data stay in registers.  With
+// PF, rows that fit one load batch are software-pipelined: the next row's
+// loads are issued before the current row is consumed.  QL <= QMAX is required: boxes with rows longer
 // than 4 * 32 * QMAX - 3 elements must be split along the last dimension.
 // ---------------------------------------------------------------------------
 struct TileShape {
@@ -504,8 +506,8 @@ __device__ __forceinline__ TileShape tile_shape(int L, int head, int nthreads, i
     return t;
 }
 
-template <int D, int QMAX, int U, typename S, typename SD, bool TWO, typename SlotFn,
-          typename RowFn, typename QuadFn>
+template <int D, int QMAX, int U, typename S, typename SD, bool TWO, bool PF = false,
+          typename SlotFn, typename RowFn, typename QuadFn>
 __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
                                           const float *__restrict__ in2, const int64_t *stride,
                                           const int *box_lo, const int *box_len, int r0, int r1,
@@ -525,8 +527,8 @@ __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
     const int64_t step = 4 * int64_t(t.LPR);
     RowIter<D> it;
     it.init(box_len, r0 + grp, t.G);
-    for (int r = r0 + grp; r < r1; r += t.G) {
-        int coords[kMaxDim];
+    // the next row of this thread: its coordinates and first quad address
+    auto next_row = [&](int *coords, int64_t &a0) {
         int64_t start = box_lo[D - 1];
 #pragma unroll
         for (int j = 0; j < D - 1; ++j) {
@@ -534,29 +536,165 @@ __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
             start += int64_t(coords[j]) * stride[j];
         }
         it.next();
+        a0 = start - t.head + 4 * gl;
+    };
+    auto load = [&](int64_t a0, int i0, float4 (&v)[U], float4 (&v2)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (ok[i0 + u]) {
+                const float4 *q = reinterpret_cast<const float4 *>(in + a0 + (i0 + u) * step);
+                v[u] = stream ? __ldcs(q) : __ldg(q);
+                if (TWO) v2[u] = __ldcs(reinterpret_cast<const float4 *>(in2 + a0 + (i0 + u) * step));
+            }
+        }
+    };
+    if (PF && t.QL <= U) {
+        // one load batch per row: the next row's loads are in flight while
+        // this row is consumed
+        int r = r0 + grp;
+        if (r >= r1) return;
+        int cc[kMaxDim];
+        int64_t ac;
+        float4 v[U], v2[U];
+        next_row(cc, ac);
+        load(ac, 0, v, v2);
+        for (;;) {
+            const int rn = r + t.G;
+            int cn[kMaxDim];
+            int64_t an = 0;
+            float4 vn[U], vn2[U];
+            if (rn < r1) {
+                next_row(cn, an);
+                load(an, 0, vn, vn2);
+            }
+            S st;
+            row_fn(cc, st);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) quad_fn(st, sd[u], u, v[u], v2[u], ac + u * step);
+            if (rn >= r1) break;
+            r = rn;
+            ac = an;
+#pragma unroll
+            for (int j = 0; j < D - 1; ++j) cc[j] = cn[j];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                v[u] = vn[u];
+                if (TWO) v2[u] = vn2[u];
+            }
+        }
+        return;
+    }
+    for (int r = r0 + grp; r < r1; r += t.G) {
+        int coords[kMaxDim];
+        int64_t a0;
+        next_row(coords, a0);
         S st;
         row_fn(coords, st);
-        const int64_t a0 = start - t.head + 4 * gl;
-        const float *p = in + a0;
-        const float *p2 = TWO ? in2 + a0 : nullptr;
 #pragma unroll
         for (int i0 = 0; i0 < QMAX; i0 += U) {
             if (i0 < t.QL) {
                 float4 v[U], v2[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (ok[i0 + u]) {
-                        const float4 *q = reinterpret_cast<const float4 *>(p + (i0 + u) * step);
-                        v[u] = stream ? __ldcs(q) : __ldg(q);
-                        if (TWO) v2[u] = __ldcs(reinterpret_cast<const float4 *>(p2 + (i0 + u) * step));
-                    }
-                }
+                load(a0, i0, v, v2);
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                     if (ok[i0 + u]) quad_fn(st, sd[i0 + u], i0 + u, v[u], v2[u], a0 + (i0 + u) * step);
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous tile walker: the same fixed quad slots as walk_tile, but each
+// thread's quads are copied global -> shared with cp.async (16 bytes per
+// copy, no registers held while in flight) into a per-thread ring of ST row
+// stages, ST - 1 rows ahead of the row being consumed; the consumer reads its
+// own stage back with 128-bit shared loads.  Ring layout [stage][slot][thread]
+// (consecutive lanes, consecutive 16 bytes: conflict-free).  The ring holds
+// ST * QMAX * blockDim float4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int D, int QMAX, int ST, typename S, typename SD, typename SlotFn, typename RowFn,
+          typename QuadFn>
+__device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, const int64_t *stride,
+                                                const int *box_lo, const int *box_len, int r0,
+                                                int r1, const TileShape &t, float4 *ring,
+                                                SlotFn slot_fn, RowFn row_fn, QuadFn quad_fn) {
+    const int gl = threadIdx.x & (t.LPR - 1), grp = threadIdx.x / t.LPR;
+    const int L = box_len[D - 1];
+    const int nt = blockDim.x;
+    bool ok[QMAX];
+    SD sd[QMAX];
+#pragma unroll
+    for (int i = 0; i < QMAX; ++i) {
+        const int e0 = 4 * (gl + i * t.LPR) - t.head;
+        ok[i] = i < t.QL && e0 < L && e0 + 4 > 0;
+        sd[i] = slot_fn(i, e0);
+    }
+    const int64_t step = 4 * int64_t(t.LPR);
+    const int first = r0 + grp;
+    const int nk = first < r1 ? (r1 - first + t.G - 1) / t.G : 0;
+    const uint32_t ring_s = uint32_t(__cvta_generic_to_shared(ring));
+    auto slot_addr = [&](int stage, int i) {
+        return ring_s + 16u * uint32_t((stage * QMAX + i) * nt + int(threadIdx.x));
+    };
+    RowIter<D> iss, con;   // rows being issued and rows being consumed
+    iss.init(box_len, first, t.G);
+    con.init(box_len, first, t.G);
+    auto row_addr = [&](RowIter<D> &it, int *coords) {
+        int64_t start = box_lo[D - 1];
+#pragma unroll
+        for (int j = 0; j < D - 1; ++j) {
+            coords[j] = box_lo[j] + it.c[j];
+            start += int64_t(coords[j]) * stride[j];
+        }
+        it.next();
+        return start - t.head + 4 * gl;
+    };
+    auto issue = [&](int stage) {
+        int coords[kMaxDim];
+        const int64_t a0 = row_addr(iss, coords);
+#pragma unroll
+        for (int i = 0; i < QMAX; ++i)
+            if (ok[i]) cp_async16(slot_addr(stage, i), in + a0 + i * step);
+    };
+#pragma unroll
+    for (int k = 0; k < ST - 1; ++k) {
+        if (k < nk) issue(k);
+        cp_async_commit();
+    }
+    int stage_c = 0, stage_i = ST - 1;
+    for (int k = 0; k < nk; ++k) {
+        if (k + ST - 1 < nk) issue(stage_i);
+        cp_async_commit();
+        cp_async_wait<ST - 1>();   // row k has landed
+        int coords[kMaxDim];
+        const int64_t a0 = row_addr(con, coords);
+        S st;
+        row_fn(coords, st);
+#pragma unroll
+        for (int i = 0; i < QMAX; ++i)
+            if (ok[i]) {
+                const float4 v = lds128(slot_addr(stage_c, i));
+                quad_fn(st, sd[i], i, v, v, a0 + i * step);
+            }
+        stage_c = (stage_c + 1 == ST) ? 0 : stage_c + 1;
+        stage_i = (stage_i + 1 == ST) ? 0 : stage_i + 1;
+    }
+    cp_async_wait<0>();
 }
 
 // shared-memory access by 32-bit shared-window address

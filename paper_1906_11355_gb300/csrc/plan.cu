@@ -34,41 +34,42 @@ int64_t n_cells(const Geom &g) {
     return c;
 }
 
-// Default launch shapes (the autotuner may replace them).
+// Default launch shapes (the autotuner may replace them).  Each CTA should
+// own enough voxels to amortise its fixed work (zeroing and summing the
+// histogram copies, building tables, staging the corner tables), which the
+// timed candidates of mclahe_autotune favour over more, smaller CTAs:
 //   histogram: G kernels per work item along the last dimension, so that an
-//   item's rows span at least 64 elements (256 bytes); R lane copies, as many
-//   as keep the CTA's shared memory within 100 KiB and the copy summation
-//   (G * P * R words) small next to the item's voxels; cluster size C, a power
-//   of two up to 8, grown while the grid is short of four CTAs per SM and
-//   every CTA keeps at least 8192 voxels;
-//   mapping: enough CTAs for several waves on the SMs, each covering at least
-//   four rows of its cell.
+//   item's rows span at least 64 elements (256 bytes); R lane copies, at most
+//   16, as many as keep the CTA's shared memory within 64 KiB and the copy
+//   summation (G * P * R words) small next to the item's voxels; cluster
+//   size C, a power of two up to 8, about one CTA per 300 Ki voxels;
+//   mapping: about one CTA per 64 Ki voxels of a cell.
 Tuning default_tuning(const Geom &g) {
     Tuning t;
     t.hist_threads = 256;
     t.map_threads = 256;
-    const int sms = 152;
     const Dim &dl = g.d[g.D - 1];
     int G = std::min(dl.n, std::max(1, (64 + dl.b - 1) / dl.b));
-    const int64_t vitem = g.V * G;
-    int R = 32;
-    while (R > 1 && (hist_smem_bytes(g, R, G) > 100 * 1024 ||
-                     int64_t(g.P) * R * G > std::max<int64_t>(vitem / 2, int64_t(g.P) * G)))
+    int R = 16;
+    while (R > 1 && (hist_smem_bytes(g, R, G) > 64 * 1024 ||
+                     int64_t(g.P) * R * G > std::max<int64_t>(g.V * G / 2, int64_t(g.P) * G)))
         R >>= 1;
     while (G > 1 && hist_smem_bytes(g, R, G) > 100 * 1024) G >>= 1;
     t.hist_group = G;
     t.hist_copies = R;
-    const int64_t items = hist_items(g, G);
+    const int64_t vitem = g.V * G;
     int C = 1;
-    while (C < 8 && items * C < 4 * sms && vitem / (2 * C) >= 8192) C <<= 1;
+    while (C < 8 && vitem / (2 * C) >= 300 * 1024) C <<= 1;
     t.hist_chunks = C;
-    int64_t rows = 1;   // rows of an interior cell
-    for (int j = 0; j + 1 < g.D; ++j) rows *= g.d[j].b;
+    int64_t rows = 1, cell_vox = dl.b;   // rows and voxels of an interior cell
+    for (int j = 0; j + 1 < g.D; ++j) {
+        rows *= g.d[j].b;
+        cell_vox *= g.d[j].b;
+    }
+    int64_t mc = (cell_vox + 65535) / 65536;
+    t.map_chunks = int(std::min<int64_t>(std::max<int64_t>(std::min(mc, rows), 1), 64));
     const int64_t cells = n_cells(g);
-    int64_t mc = (int64_t(sms) * 8 + cells - 1) / cells;
-    mc = std::min<int64_t>(std::max<int64_t>(mc, 1), std::max<int64_t>(rows / 4, 1));
-    t.map_chunks = int(std::min<int64_t>(mc, 64));
-    int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
+    int64_t bc = (int64_t(152) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
     t.bwd_chunks = int(std::min<int64_t>(bc, 32));
     return t;
@@ -203,7 +204,7 @@ mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
     }
     // the 2^D neighbouring tables and one histogram (one lane copy at the
     // least) must fit in a CTA's shared memory
-    if (map_smem_bytes(g) > 200 * 1024 || hist_smem_bytes(g, 1, 1) > 200 * 1024)
+    if (map_smem_bytes(g) > 220 * 1024 || hist_smem_bytes(g, 1, 1) > 220 * 1024)
         return MCLAHE_ERR_UNSUPPORTED;
     // CTAs per footprint row range: counts must stay in 32 bits
     int64_t foot = 1;

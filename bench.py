@@ -164,9 +164,12 @@ def algorithmic_bytes(info, adaptive, has_range):
 
 
 def kernel_source_hash(pass_name):
-    fn = {"range": "k_range.cu", "hist": "k_hist.cu", "map": "k_map.cu"}[pass_name]
+    """Hash of the sources a pass's kernel is compiled from (the recorded ncu
+    traffic is only reported while this matches)."""
+    files = {"range": ("k_range.cu",), "hist": ("k_hist.cu", "hist_impl.cuh"),
+             "map": ("k_map.cu", "map_impl.cuh")}[pass_name]
     h = hashlib.sha256()
-    for f in (fn, "mclahe_internal.cuh"):
+    for f in files + ("mclahe_internal.cuh",):
         with open(os.path.join(ROOT, "paper_1906_11355_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -295,6 +295,10 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     const int nb = g.nb, P = g.P;
     const int lane = threadIdx.x & 31;
     const Dim &dl = g.d[D - 1];
+    // a one-CTA cluster needs only block barriers
+    auto csync = [&]() {
+        if (C > 1) cluster.sync(); else __syncthreads();
+    };
     const int n_groups = (dl.n + G - 1) / G;
 
     // item -> outer kernel coordinates and the group along the last dim
@@ -489,11 +493,11 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                 });
             }
         });
-        cluster.sync();   // every CTA's keys are complete
+        csync();   // every CTA's keys are complete
         for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
             uint32_t a = 0, b = 0;
             for (int c = 0; c < C; ++c) {
-                const uint32_t *rk = cluster.map_shared_rank(s_keys, c);
+                const uint32_t *rk = C > 1 ? cluster.map_shared_rank(s_keys, c) : s_keys;
                 a = max(a, rk[2 * kg]);
                 b = max(b, rk[2 * kg + 1]);
             }
@@ -642,7 +646,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         const int kg = t / (P - nb), j = nb + t % (P - nb);
         atomicAdd(&cnt[kg * P + nb - 1], cnt[kg * P + j]);
     }
-    cluster.sync();   // every CTA's counts are complete
+    csync();   // every CTA's counts are complete
 
     // ---- phase 4: rank r owns kernels r, r + C, ...: sums the CTAs' counts
     // in rank order, stores the histogram, builds the mapping table
@@ -650,7 +654,11 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         uint32_t *ck = cnt + size_t(kg) * P;
         for (int j = threadIdx.x; j < nb; j += blockDim.x) {
             uint32_t s = 0;
-            for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
+            if (C > 1) {
+                for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
+            } else {
+                s = ck[j];
+            }
             ck[j] = s;
         }
         __syncthreads();
@@ -663,7 +671,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
             scale_out[k] = s_sc[kg];
         }
     }
-    cluster.sync();   // the other CTAs' shared memory is no longer read
+    csync();   // the other CTAs' shared memory is no longer read
 }
 
 }  // namespace mclahe

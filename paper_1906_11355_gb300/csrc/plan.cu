@@ -43,7 +43,9 @@ int64_t n_cells(const Geom &g) {
 //   16, as many as keep the CTA's shared memory within 64 KiB and the copy
 //   summation (G * P * R words) small next to the item's voxels; cluster
 //   size C, a power of two up to 8, about one CTA per 300 Ki voxels;
-//   mapping: about one CTA per 64 Ki voxels of a cell.
+//   mapping: about one CTA per 64 Ki voxels of a cell;
+//   both raised to give small volumes at least one CTA per SM while every CTA
+//   keeps some thousands of voxels.
 Tuning default_tuning(const Geom &g) {
     Tuning t;
     t.hist_threads = 256;
@@ -57,19 +59,25 @@ Tuning default_tuning(const Geom &g) {
     while (G > 1 && hist_smem_bytes(g, R, G) > 100 * 1024) G >>= 1;
     t.hist_group = G;
     t.hist_copies = R;
-    const int64_t vitem = g.V * G;
+    const int sms = 152;
+    const int64_t vitem = g.V * G, items = hist_items(g, G);
     int C = 1;
-    while (C < 8 && vitem / (2 * C) >= 300 * 1024) C <<= 1;
+    // about one CTA per 300 Ki voxels, and at least one CTA per SM while the
+    // CTAs keep 16 Ki voxels or more
+    while (C < 8 && (vitem / (2 * C) >= 300 * 1024 ||
+                     (items * C < sms && vitem / (2 * C) >= 16 * 1024)))
+        C <<= 1;
     t.hist_chunks = C;
     int64_t rows = 1, cell_vox = dl.b;   // rows and voxels of an interior cell
     for (int j = 0; j + 1 < g.D; ++j) {
         rows *= g.d[j].b;
         cell_vox *= g.d[j].b;
     }
-    int64_t mc = (cell_vox + 65535) / 65536;
-    t.map_chunks = int(std::min<int64_t>(std::max<int64_t>(std::min(mc, rows), 1), 64));
     const int64_t cells = n_cells(g);
-    int64_t bc = (int64_t(152) * 4 + cells - 1) / cells;
+    int64_t mc = (cell_vox + 65535) / 65536;
+    while (cells * mc < sms && cell_vox / (mc + 1) >= 8 * 1024) ++mc;
+    t.map_chunks = int(std::min<int64_t>(std::max<int64_t>(std::min(mc, rows), 1), 64));
+    int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
     t.bwd_chunks = int(std::min<int64_t>(bc, 32));
     return t;

@@ -35,8 +35,14 @@ DEFAULT_WORKLOAD = "3d-fluorescence-64x512x512"
 L2_FLUSH_BYTES = 256 << 20
 PEAK_FALLBACK_GBS = 6800.0
 
-# kernel launched by each pass (for the roofline and the ncu launch list)
-PASS_KERNEL = {"range": "k_range_global", "hist": "k_hist", "map": "k_map"}
+def pass_kernel(pass_name, info):
+    """Kernel launched by a pass (for the roofline and the ncu launch list)."""
+    flat = info["hist_shares"] > 0
+    if pass_name == "range":
+        return "k_hist_flat" if (flat and info["mode"] == 1) else "k_range_global"
+    return {"hist": "k_hist_flat" if flat else "k_hist",
+            "map": "k_map_tma" if info["map_tma"] else "k_map"}[pass_name]
+
 
 
 def parse():
@@ -150,13 +156,19 @@ def algorithmic_bytes(info, adaptive, has_range):
     """Bytes each pass must move at least: the range pass reads the input once
     (a global range not given by the caller); the histogram pass reads the
     input once and writes the histograms, tables and ranges; the mapping pass
-    reads the input and writes the output (4 B per voxel each)."""
+    reads the input and writes the output (4 B per voxel each).  With the
+    adaptive range the flat histogram form has a range pass of its own, which
+    reads the input once."""
     N = info["n_voxels"]
     K = info["n_kernels"]
     nb = info["n_bins"]
     ls = info["table_stride"]
+    if adaptive:   # the flat form's range pass writes every kernel's min/max keys
+        rng = 4 * N + 8 * K if info["hist_shares"] > 0 else 0
+    else:
+        rng = 0 if has_range else 4 * N
     return {
-        "range": 0 if (adaptive or has_range) else 4 * N,
+        "range": rng,
         "hist": 4 * N + 4 * K * nb + 4 * K * ls + 8 * K,
         "lut": 0,
         "map": 8 * N,
@@ -166,8 +178,8 @@ def algorithmic_bytes(info, adaptive, has_range):
 def kernel_source_hash(pass_name):
     """Hash of the sources a pass's kernel is compiled from (the recorded ncu
     traffic is only reported while this matches)."""
-    files = {"range": ("k_range.cu",), "hist": ("k_hist.cu", "hist_impl.cuh"),
-             "map": ("k_map.cu", "map_impl.cuh")}[pass_name]
+    files = {"range": ("k_range.cu", "k_hist.cu", "hist_impl.cuh"), "hist": ("k_hist.cu", "hist_impl.cuh"),
+             "map": ("k_map.cu", "map_impl.cuh", "tma.cuh")}[pass_name]
     h = hashlib.sha256()
     for f in files + ("mclahe_internal.cuh",):
         with open(os.path.join(ROOT, "paper_1906_11355_gb300", "csrc", f), "rb") as fh:
@@ -351,7 +363,7 @@ def measure_fwd_bwd(dev, steps, warmup):
     g.manual_seed(4)
     clips = (0.005 + 0.045 * torch.rand(B, generator=g)).to(dev)
     op = MCLAHE(shape, ks, nb, 0.02, adaptive=True, device=dev)
-    wss = [torch.empty(op.ws_bytes, dtype=torch.uint8, device=dev) for _ in range(B)]
+    wss = [torch.zeros(op.ws_bytes, dtype=torch.uint8, device=dev) for _ in range(B)]
     outs = [torch.empty_like(x) for x in xs]
     gouts = [torch.empty_like(x) for x in xs]
     gclip = torch.empty(B, dtype=torch.float32, device=dev)
@@ -417,7 +429,8 @@ def run_native(args):
     if not args.no_autotune:
         op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
     shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
-              if k in ("hist_group", "hist_cluster", "hist_copies", "map_chunks", "tuned")}
+              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "map_chunks",
+                       "map_tma", "tuned")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     passes = list(range(nat.MCLAHE_N_PASSES))
@@ -491,12 +504,14 @@ def run_native(args):
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peak_gbs()
-    algo = algorithmic_bytes(op.info, w["adaptive"], False)
-    kern = {k: v for k, v in pass_ms.items() if k in PASS_KERNEL and launches[nat.PASS_NAMES.index(k)] > 0}
+    info = nat.mclahe_plan_query(op.plan)   # launch shapes after autotuning
+    algo = algorithmic_bytes(info, w["adaptive"], False)
+    kern = {k: v for k, v in pass_ms.items()
+            if k in ("range", "hist", "map") and launches[nat.PASS_NAMES.index(k)] > 0}
     dom = max(kern, key=kern.get)
     achieved = algo[dom] / (pass_ms[dom] * 1e-3) / 1e9
     traffic = recorded_traffic(args.workload, dom)
-    roofline = {"bound": "hbm", "kernel": PASS_KERNEL[dom], "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": pass_kernel(dom, info), "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_kind": peak_kind, "algorithmic_bytes": algo[dom]}
     whole = 12 * voxels / (ms * 1e-3) / 1e9    # 2 input reads + 1 output write

@@ -26,7 +26,8 @@
  *     errors are returned synchronously and leave the device untouched.
  *     A failed kernel launch returns MCLAHE_ERR_CUDA.  Errors found by device
  *     code are written to the status word at the start of the workspace and
- *     are read back by mclahe_sync_status().
+ *     are read back by mclahe_sync_status(); a new workspace must start with
+ *     that word zero (allocate it zeroed, or call mclahe_sync_status once).
  *   - Readings of points the paper leaves open:
  *       padding length p = 2b - 1 - ((s - 1) mod b) (Eq. (1); Algorithm 1's
  *         first step prints "+", which cannot make s + p a multiple of b);
@@ -100,7 +101,8 @@ typedef struct {
                                      entries past n_bins - 1 repeat it) */
     /* byte offsets inside the workspace (all 256-byte aligned) */
     size_t ws_status;             /* uint32 status word */
-    size_t ws_range_keys;         /* uint32 [2 or 2K] order-preserving min/max keys */
+    size_t ws_range_keys;         /* uint32 [2 + 2K] order-preserving min/max keys: the global
+                                     range, then each kernel's adaptive range (flat pass) */
     size_t ws_hist;               /* uint32 [K][n_bins] kernel histograms */
     size_t ws_lo;                 /* float  [K] histogram range start per kernel */
     size_t ws_scale;              /* float  [K] histogram scale per kernel */
@@ -113,7 +115,16 @@ typedef struct {
     int32_t hist_copies;          /* lane copies of the shared-memory histograms */
     int32_t map_chunks;           /* CTAs per inter-kernel cell in the mapping pass */
     int32_t bwd_chunks;           /* CTAs per inter-kernel cell in the backward pass */
-    int32_t tuned;                /* 1 if the shapes come from mclahe_autotune */
+    int32_t tuned;                /* 1 if the shapes come from mclahe_autotune, 2 if from
+                                     mclahe_plan_set_shapes, else 0 */
+    int32_t hist_shares;          /* > 0: the histogram pass is flat: every work item is cut
+                                     into hist_shares equal shares of its rows, dealt out in
+                                     order to a persistent grid (hist_cluster is then 1);
+                                     0: one cluster per work item */
+    int32_t hist_ctas;            /* CTAs of the flat histogram pass at its last launch (0 if
+                                     not flat or not launched yet) */
+    int32_t map_tma;              /* 1: the mapping pass streams its cells as TMA box tiles */
+    int32_t reserved;
 } mclahe_plan_info;
 
 /*
@@ -167,10 +178,15 @@ MCLAHE_API mclahe_status mclahe_forward(mclahe_plan_t plan, const float *d_in, f
 
 /* The passes of mclahe_forward, in the order it runs them. */
 typedef enum {
-    MCLAHE_PASS_CLEAR = 0,  /* zero the global range keys (memset; nothing else needs it) */
-    MCLAHE_PASS_RANGE = 1,  /* global range, Sec. III.D (launches only for GHR without a range) */
-    MCLAHE_PASS_HIST = 2,   /* adaptive ranges, per-kernel histograms, clip, redistribute,
-                               CDF and normalisation (Algorithm 1), one cluster per kernel */
+    MCLAHE_PASS_CLEAR = 0,  /* zero what later passes accumulate with atomics (memset): the
+                               global range keys; in the flat histogram form also the
+                               per-kernel range keys, work-item tickets and histograms */
+    MCLAHE_PASS_RANGE = 1,  /* global range, Sec. III.D (GHR without a given range), or each
+                               kernel's adaptive range (AHR, flat histogram form) */
+    MCLAHE_PASS_HIST = 2,   /* per-kernel histograms (with AHR in the cluster form also their
+                               ranges), clip, redistribute, CDF and normalisation
+                               (Algorithm 1): one cluster per group of kernels, or the flat
+                               form (equal row shares over a persistent grid) */
     MCLAHE_PASS_LUT = 3,    /* no work: the tables are built by MCLAHE_PASS_HIST */
     MCLAHE_PASS_MAP = 4,    /* multilinear mapping, Sec. III.C, Eq. (12)-(13) */
     MCLAHE_N_PASSES = 5
@@ -241,6 +257,27 @@ MCLAHE_API size_t mclahe_batch_workspace_bytes(int n_vol, const mclahe_plan_t *p
  */
 MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, float *d_out, void *d_ws,
                               size_t ws_bytes, mclahe_stream_t stream);
+
+/*
+ * mclahe_plan_set_shapes -- set the plan's launch shapes explicitly (host
+ * only; no CUDA call), e.g. shapes a previous process's mclahe_autotune picked
+ * (read back with mclahe_plan_query).  No counterpart in the paper: shapes
+ * change how the work is split, never the result.
+ *   hist_group    kernels along the last dim per histogram work item, 1..n_last.
+ *   hist_cluster  CTAs per work item (a cluster): 1, 2, 4 or 8; 1 if hist_shares > 0.
+ *   hist_copies   lane copies of the shared-memory histograms: 1, 2, 4, ..., 32.
+ *   hist_shares   0: cluster form; 1..4096: flat form with that many shares per item.
+ *   map_chunks    CTAs per inter-kernel cell in the mapping pass, 1..64.
+ *   map_tma       0: per-thread loads and stores; 1: TMA box tiles (3- and 4-D volumes
+ *                 whose last dim and cell rows start on 16-byte boundaries only).
+ * Returns MCLAHE_ERR_INVALID_ARG (plan unchanged) for values outside these
+ * ranges, a histogram CTA above 220 KiB of shared memory, or map_tma = 1 on a
+ * geometry that does not allow it.  Sets tuned = 2.
+ */
+MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist_group,
+                                                int32_t hist_cluster, int32_t hist_copies,
+                                                int32_t hist_shares, int32_t map_chunks,
+                                                int32_t map_tma);
 
 /* Size of the library's built-in scratch array used by mclahe_forward_noalloc. */
 #define MCLAHE_NOALLOC_SCRATCH_BYTES (8u << 20)

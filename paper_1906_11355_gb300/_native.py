@@ -33,6 +33,7 @@ EXPORTS = (
     "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
+    "mclahe_plan_set_shapes",
 )
 
 MCLAHE_NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -57,6 +58,8 @@ class PlanInfo(ctypes.Structure):
         ("hist_group", ctypes.c_int32), ("hist_cluster", ctypes.c_int32),
         ("hist_copies", ctypes.c_int32), ("map_chunks", ctypes.c_int32),
         ("bwd_chunks", ctypes.c_int32), ("tuned", ctypes.c_int32),
+        ("hist_shares", ctypes.c_int32), ("hist_ctas", ctypes.c_int32),
+        ("map_tma", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -120,6 +123,8 @@ def load(path: str = LIB_PATH):
         lib.mclahe_pass_launches.restype = ctypes.c_int
         lib.mclahe_forward_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.mclahe_forward_noalloc.restype = ctypes.c_int
+        lib.mclahe_plan_set_shapes.argtypes = [vp] + [ctypes.c_int32] * 6
+        lib.mclahe_plan_set_shapes.restype = ctypes.c_int
         lib.mclahe_version.argtypes = []
         lib.mclahe_version.restype = ctypes.c_int
         _lib = lib
@@ -200,6 +205,14 @@ def mclahe_plan_query(plan) -> dict:
     info = PlanInfo()
     _check(load().mclahe_plan_query(plan.handle, ctypes.byref(info)), "mclahe_plan_query")
     return info.as_dict()
+
+
+def mclahe_plan_set_shapes(plan, hist_group, hist_cluster, hist_copies, hist_shares, map_chunks,
+                           map_tma=0):
+    _check(load().mclahe_plan_set_shapes(plan.handle, int(hist_group), int(hist_cluster),
+                                         int(hist_copies), int(hist_shares), int(map_chunks),
+                                         int(map_tma)),
+           "mclahe_plan_set_shapes")
 
 
 def mclahe_workspace_bytes(plan) -> int:

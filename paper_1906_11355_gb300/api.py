@@ -33,7 +33,7 @@ class MCLAHE:
         self.info = nat.mclahe_plan_query(self.plan)
         self.device = torch.device(device)
         self.ws_bytes = nat.mclahe_workspace_bytes(self.plan)
-        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
     @property
     def n_kernels(self):
@@ -63,6 +63,18 @@ class MCLAHE:
         if out is None:
             out = torch.empty_like(x)
         nat.mclahe_autotune(self.plan, x, out, self.ws, self.ws_bytes, stream)
+
+    def shapes(self):
+        """The plan's launch shapes (to reuse them with set_shapes)."""
+        info = nat.mclahe_plan_query(self.plan)
+        return {k: int(info[k]) for k in ("hist_group", "hist_cluster", "hist_copies",
+                                          "hist_shares", "map_chunks", "map_tma")}
+
+    def set_shapes(self, hist_group, hist_cluster, hist_copies, hist_shares, map_chunks,
+                   map_tma=0):
+        """Set launch shapes explicitly (e.g. from another process's autotune)."""
+        nat.mclahe_plan_set_shapes(self.plan, hist_group, hist_cluster, hist_copies, hist_shares,
+                                   map_chunks, map_tma)
 
     # views into the workspace left by the last forward call
     def _view(self, key, count, dtype):
@@ -119,7 +131,7 @@ class MCLAHEBatch:
                                               s.get("clip_limit", 0.01), mode, s.get("global_range")))
         self.device = torch.device(device)
         self.ws_bytes = nat.mclahe_batch_workspace_bytes(self.plans)
-        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
     def forward(self, xs, outs=None, clip=None, stream=None, use_graph=True):
         """Run MCLAHE on every volume of xs (contiguous float32 CUDA tensors);

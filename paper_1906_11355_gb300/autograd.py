@@ -25,7 +25,7 @@ class MCLAHEFunction(torch.autograd.Function):
     def forward(ctx, x, clip, op):
         op._check_volume(x)
         clip = clip.reshape(1).contiguous()
-        ws = torch.empty(op.ws_bytes, dtype=torch.uint8, device=x.device)
+        ws = torch.zeros(op.ws_bytes, dtype=torch.uint8, device=x.device)
         out = torch.empty_like(x)
         nat.mclahe_forward(op.plan, x, out, ws, op.ws_bytes, clip)
         ctx.save_for_backward(x, clip)

@@ -2,9 +2,12 @@
 // timing candidates on the caller's buffers (no counterpart in the paper).
 //
 // Histogram pass: kernels per work item G in {1, 2, 4, ...} and the whole
-// last dimension x cluster size C in {1, 2, 4, 8} x lane copies R in
-// {2, 4, 8, 16, 32} (shared memory at most 160 KiB).  Mapping pass: CTAs per cell
-// in {1, 2, 4, ..., 64} (at most one row per CTA).  Each candidate runs twice
+// last dimension x lane copies R in {2, 4, 8, 16, 32} (shared memory with the
+// row ring at most 200 KiB) x form: a cluster of C in {1, 2, 4, 8} CTAs per
+// item, or the flat form with S in {1, 2, 4, ..., 256} shares per item (with
+// its range pass, under the adaptive range).  Mapping pass: per-thread loads
+// or TMA tiles (where the geometry allows) x CTAs per cell in {1, 2, 4, ...,
+// 64} (at most one row per CTA).  Each candidate runs twice
 // after one warm-up and keeps its faster time; results are cached per
 // (shape, kernel size, n_bins, range mode, given range) for the process, so a
 // later plan of the same problem takes them without timing.
@@ -35,15 +38,20 @@ TuneKey tune_key(const mclahe_plan_s &p) {
     return TuneKey(p.g.D, dims, p.g.nb, p.g.mode, p.g.has_range);
 }
 
-// Seconds of the best of two timed runs of one pass (after a warm-up), or a
-// negative value if a launch fails.
-float time_pass(mclahe_plan_s &p, int pass, const float *in, float *out, unsigned char *ws,
-                cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-    if (run_pass(p, pass, in, out, ws, nullptr, st) != MCLAHE_OK) return -1.0f;
+// Milliseconds of the best of two timed runs of passes [p0, p1] (after a
+// warm-up), or a negative value if a launch fails.
+float time_passes(mclahe_plan_s &p, int p0, int p1, const float *in, float *out,
+                  unsigned char *ws, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    auto run = [&]() {
+        for (int pass = p0; pass <= p1; ++pass)
+            if (run_pass(p, pass, in, out, ws, nullptr, st) != MCLAHE_OK) return false;
+        return true;
+    };
+    if (!run()) return -1.0f;
     float best = 1e30f;
     for (int r = 0; r < 2; ++r) {
         cudaEventRecord(e0, st);
-        if (run_pass(p, pass, in, out, ws, nullptr, st) != MCLAHE_OK) return -1.0f;
+        if (!run()) return -1.0f;
         cudaEventRecord(e1, st);
         if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0f;
         float ms = 0.0f;
@@ -86,28 +94,38 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
     const Tuning t0 = p->t;
     Tuning best = t0;
     s = MCLAHE_OK;
-    // the range (if any) feeds the histogram pass
-    if (run_pass(*p, MCLAHE_PASS_CLEAR, d_in, d_out, ws, nullptr, st) != MCLAHE_OK ||
-        run_pass(*p, MCLAHE_PASS_RANGE, d_in, d_out, ws, nullptr, st) != MCLAHE_OK)
-        s = MCLAHE_ERR_CUDA;
     float best_ms = 1e30f;
     std::vector<int> groups;
     const int nl = p->g.d[p->g.D - 1].n;
     for (int G = 1; G < nl; G <<= 1) groups.push_back(G);
     groups.push_back(nl);
+    // every candidate is timed with the passes that feed it (the clear, and
+    // the range pass: the flat form's adaptive range is its own pass)
+    int64_t item_rows = 1;
+    for (int j = 0; j + 1 < p->g.D; ++j) item_rows *= p->g.d[j].b;
     for (int G : groups) {
-        for (int C = 1; C <= 8 && s == MCLAHE_OK; C <<= 1) {
-            for (int R = 2; R <= 32; R <<= 1) {
-                if (hist_smem_bytes(p->g, R, G) > 160 * 1024) continue;
-                p->t.hist_group = G;
-                p->t.hist_chunks = C;
-                p->t.hist_copies = R;
-                const float ms = time_pass(*p, MCLAHE_PASS_HIST, d_in, d_out, ws, st, e0, e1);
+        for (int R = 2; R <= 32 && s == MCLAHE_OK; R <<= 1) {
+            if (hist_smem_bytes(p->g, R, G) > 200 * 1024) continue;
+            p->t.hist_group = G;
+            p->t.hist_copies = R;
+            // cluster form: C CTAs per item; flat form: S shares per item
+            for (int v = 0; v < 4 + 9; ++v) {
+                if (v < 4) {
+                    p->t.hist_chunks = 1 << v;
+                    p->t.hist_shares = 0;
+                } else {
+                    p->t.hist_chunks = 1;
+                    p->t.hist_shares = 1 << (v - 4);
+                    if (p->t.hist_shares > item_rows) continue;
+                }
+                const float ms = time_passes(*p, MCLAHE_PASS_CLEAR, MCLAHE_PASS_HIST, d_in, d_out,
+                                             ws, st, e0, e1);
                 if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
                 if (ms < best_ms) {
                     best_ms = ms;
                     best.hist_group = G;
-                    best.hist_chunks = C;
+                    best.hist_chunks = p->t.hist_chunks;
+                    best.hist_shares = p->t.hist_shares;
                     best.hist_copies = R;
                 }
             }
@@ -118,16 +136,24 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
     if (s == MCLAHE_OK) {
         p->t = best;
         // tables for the mapping candidates
-        if (run_pass(*p, MCLAHE_PASS_HIST, d_in, d_out, ws, nullptr, st) != MCLAHE_OK) s = MCLAHE_ERR_CUDA;
+        for (int pass = MCLAHE_PASS_CLEAR; pass <= MCLAHE_PASS_HIST; ++pass)
+            if (run_pass(*p, pass, d_in, d_out, ws, nullptr, st) != MCLAHE_OK) s = MCLAHE_ERR_CUDA;
         int64_t rows = 1;
         for (int j = 0; j + 1 < p->g.D; ++j) rows *= p->g.d[j].b;
         best_ms = 1e30f;
-        for (int mc = 1; mc <= 64 && mc <= rows && s == MCLAHE_OK; mc <<= 1) {
-            p->t.map_chunks = mc;
-            const float ms = time_pass(*p, MCLAHE_PASS_MAP, d_in, d_out, ws, st, e0, e1);
-            if (ms >= 0.0f && ms < best_ms) {
-                best_ms = ms;
-                best.map_chunks = mc;
+        int bx, by, bz;
+        const int n_walks = map_tma_box(p->g, bx, by, bz) ? 2 : 1;
+        for (int tma = 0; tma < n_walks; ++tma) {
+            p->t.map_tma = tma;
+            for (int mc = 1; mc <= 64 && mc <= rows && s == MCLAHE_OK; mc <<= 1) {
+                p->t.map_chunks = mc;
+                const float ms =
+                    time_passes(*p, MCLAHE_PASS_MAP, MCLAHE_PASS_MAP, d_in, d_out, ws, st, e0, e1);
+                if (ms >= 0.0f && ms < best_ms) {
+                    best_ms = ms;
+                    best.map_chunks = mc;
+                    best.map_tma = tma;
+                }
             }
         }
         cudaGetLastError();

@@ -153,7 +153,7 @@ mclahe_status enqueue_batch(int n_vol, const mclahe_plan_t *plans, const float *
             nr[i] = B.n_range;
             nk[i] = B.n_hist;
             nc[i] = n_cells(p.g) * B.mgroups;
-            smem = std::max(smem, std::max(hist_smem_bytes(p.g, B.R, B.G), map_smem_for(p.g.D, p.g.P, false)));
+            smem = std::max(smem, std::max(hist_smem_bytes(p.g, B.R, B.G, false), map_smem_for(p.g.D, p.g.P, false)));
         }
         // the group's counters: 2 per volume, by group-local index
         bp->done = reinterpret_cast<uint32_t *>(ws + L.done + 8 * i0);

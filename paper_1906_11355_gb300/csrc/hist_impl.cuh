@@ -220,6 +220,67 @@ __device__ __forceinline__ void block_lut(const uint32_t *h, int nb, int LS, int
     for (int j = nb + int(threadIdx.x); j < LS; j += blockDim.x) out[j] = st.flat ? 0.0f : 1.0f;
 }
 
+// The same table built by one warp (lane l owns bins l, l + 32, ...; a warp
+// scan per 32 bins carries the prefixes), so the warps of a block build
+// several kernels' tables at once.  The statistics are the same integers and
+// the same float operations as block_lut's: the tables are identical.
+__device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int64_t V, float clip,
+                                         float *__restrict__ out) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    LutStats st;
+    clip_threshold(clip, V, st.tf, st.tr);
+    uint32_t nc = 0, su = 0;
+    for (int j = lane; j < nb; j += 32) {
+        const uint32_t v = h[j];
+        if (int64_t(v) > st.tf) nc += 1; else su += v;
+    }
+    st.S_tot = __reduce_add_sync(full, su);
+    st.N_c = __reduce_add_sync(full, nc);
+    const uint32_t v0 = h[0];
+    st.S0 = (int64_t(v0) > st.tf) ? 0 : v0;
+    st.A0 = (int64_t(v0) > st.tf) ? 1 : 0;
+    const int64_t H_c = V - st.S_tot;
+    const float E = __fsub_rn(float(H_c - st.N_c * st.tf), __fmul_rn(float(st.N_c), st.tr));
+    st.Eb = __fdiv_rn(E, float(nb));
+    st.flat = (st.N_c == 0) && (st.S_tot == st.S0);
+    st.den = st.diff(st.S_tot, st.N_c, nb - 1);
+    int64_t cs = 0, ca = 0;   // S and A over the earlier chunks
+    for (int j0 = 0; j0 < nb; j0 += 32) {
+        const int j = j0 + lane;
+        const uint32_t v = j < nb ? h[j] : 0u;
+        const bool over = j < nb && int64_t(v) > st.tf;
+        uint32_t s = over ? 0u : v, a = over ? 1u : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t xs = __shfl_up_sync(full, s, o);
+            const uint32_t xa = __shfl_up_sync(full, a, o);
+            if (lane >= o) {
+                s += xs;
+                a += xa;
+            }
+        }
+        if (j < nb) out[j] = st.flat ? 0.0f : __fdiv_rn(st.diff(cs + s, ca + a, j), st.den);
+        cs += __shfl_sync(full, s, 31);
+        ca += __shfl_sync(full, a, 31);
+    }
+    for (int j = nb + lane; j < LS; j += 32) out[j] = st.flat ? 0.0f : 1.0f;
+}
+
+// Tables of n kernels whose histograms lie in shared memory at h + i * P:
+// one block-wide build for a single kernel, else one warp per kernel.
+__device__ __forceinline__ void build_luts(const uint32_t *h, int P, int n, int nb, int LS, int64_t V,
+                                           float clip, float *__restrict__ lut, int64_t k0,
+                                           int64_t kstep) {
+    if (n == 1) {
+        block_lut(h, nb, LS, V, clip, lut + k0 * LS);
+        return;
+    }
+    const int nw = int(blockDim.x >> 5), warp = int(threadIdx.x >> 5);
+    for (int i = warp; i < n; i += nw)
+        warp_lut(h + size_t(i) * P, nb, LS, V, clip, lut + (k0 + i * kstep) * LS);
+}
+
 // ---------------------------------------------------------------------------
 // Work item of the histogram pass: a group of G consecutive kernels along the
 // last (contiguous) dimension, at fixed kernel coordinates along the others.
@@ -231,6 +292,15 @@ __device__ __forceinline__ void block_lut(const uint32_t *h, int nb, int LS, int
 // ---------------------------------------------------------------------------
 __host__ __device__ inline size_t hist_smem_words(int P, int R, int G) {
     return size_t(G) * P * R + size_t(G) * P + 5 * size_t(G);
+}
+// With RING, the rows of a box stream through a cp.async ring behind these
+// words (walk_tile_async: kHistStages row stages of kHistQmax quads per
+// thread), so two rows per thread are in flight while one is counted.
+constexpr int kHistQmax = 4;     // quad slots per thread and row in the histogram pass
+constexpr int kHistStages = 3;
+__host__ __device__ inline size_t hist_ring_offset_words(size_t words) { return (words + 3) & ~size_t(3); }
+__host__ __device__ inline size_t hist_ring_bytes(int nthreads) {
+    return size_t(kHistStages) * kHistQmax * size_t(nthreads) * 16;
 }
 
 // Kernels (relative to kl0, among [kl0, kl1)) that hold an image of the
@@ -279,25 +349,44 @@ __device__ __forceinline__ Targets last_targets(const Dim &d, int x, int kl0, in
     return t;
 }
 
-constexpr int kHistQmax = 4;   // quad slots per thread and row in the histogram pass
+// Modes of hist_group:
+//   kHistCluster   one thread-block cluster per item (phases 1-4 below; the
+//                  ranks split the rows, merge through DSMEM, build the tables);
+//   kHistFlat      shares [c0, c1) of `nchunks` of an item (the same fraction
+//                  of the rows of every box) in the flat persistent pass: the
+//                  CTA adds its counts to the global histograms with integer
+//                  atomics and bumps the item's ticket by c1 - c0; the CTA that
+//                  completes the ticket builds the item's tables from the
+//                  global histograms.  Adaptive ranges come from the per-kernel
+//                  keys the range pass left;
+//   kHistMinMax    that range pass: min/max of the same shares, added to the
+//                  per-kernel keys with atomic max.
+constexpr int kHistCluster = 0, kHistFlat = 1, kHistMinMax = 2;
 
-template <int D, bool ADAPTIVE>
+template <int D, bool ADAPTIVE, int MODE = kHistCluster, bool RING = false>
 __device__ __forceinline__ void hist_group(const Geom &g, const float *__restrict__ in,
                                            const uint32_t *__restrict__ keys,
                                            const float *__restrict__ d_clip,
                                            uint32_t *__restrict__ hist, float *__restrict__ lut,
                                            float *__restrict__ lo_out,
                                            float *__restrict__ scale_out, int64_t item, int G,
-                                           int R, uint32_t *sh) {
+                                           int R, uint32_t *sh, int c0 = 0, int c1 = 1,
+                                           int nchunks = 1,
+                                           uint32_t *__restrict__ tickets = nullptr,
+                                           uint32_t *__restrict__ kkeys = nullptr) {
     cg::cluster_group cluster = cg::this_cluster();
-    const int C = int(cluster.num_blocks());
-    const int rank = int(cluster.block_rank());
+    const int C = MODE == kHistCluster ? int(cluster.num_blocks()) : 1;
+    const int rank = MODE == kHistCluster ? int(cluster.block_rank()) : 0;
+    // this CTA's shares of the rows of every box
+    const int sh0 = MODE == kHistCluster ? rank : c0;
+    const int sh1 = MODE == kHistCluster ? rank + 1 : c1;
+    const int nsh = MODE == kHistCluster ? C : nchunks;
     const int nb = g.nb, P = g.P;
     const int lane = threadIdx.x & 31;
     const Dim &dl = g.d[D - 1];
     // a one-CTA cluster needs only block barriers
     auto csync = [&]() {
-        if (C > 1) cluster.sync(); else __syncthreads();
+        if (MODE == kHistCluster && C > 1) cluster.sync(); else __syncthreads();
     };
     const int n_groups = (dl.n + G - 1) / G;
 
@@ -317,14 +406,16 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     const int64_t kfirst = outer * dl.n + kl0;   // flat index of the group's first kernel
 
     // smem: copies [G][P][R], counts [G][P], keys [2G], -lo [G], scale [G], lo [G]
-    uint32_t *cnt = sh + size_t(G) * P * R;
-    uint32_t *s_keys = cnt + size_t(G) * P;
+    // (the range pass keeps only the keys and the ranges)
+    constexpr bool kKeysOnly = MODE == kHistMinMax;
+    uint32_t *cnt = sh + (kKeysOnly ? 0 : size_t(G) * P * R);
+    uint32_t *s_keys = cnt + (kKeysOnly ? 0 : size_t(G) * P);
     float *s_nlo = reinterpret_cast<float *>(s_keys + 2 * G);
     float *s_sc = s_nlo + G;
     float *s_lo = s_sc + G;
     {
         uint4 *z = reinterpret_cast<uint4 *>(sh);
-        const int nw = int(hist_smem_words(P, R, G));
+        const int nw = kKeysOnly ? 5 * G : int(hist_smem_words(P, R, G));
         for (int i = threadIdx.x; i < nw / 4; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
         for (int i = (nw / 4) * 4 + threadIdx.x; i < nw; i += blockDim.x) sh[i] = 0;
     }
@@ -369,8 +460,8 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                 w *= pc[j].m[i];
                 rows *= len[j];
             }
-            const int r0 = int((int64_t(rows) * rank) / C);
-            const int r1 = int((int64_t(rows) * (rank + 1)) / C);
+            const int r0 = int((int64_t(rows) * sh0) / nsh);
+            const int r1 = int((int64_t(rows) * sh1) / nsh);
             if (r1 <= r0) continue;
             if (single) {
                 for (int i = 0; i < pl.n; ++i)
@@ -409,8 +500,24 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         }
     };
 
+    // rows [r0, r1) of a box in fixed quad slots (walk_tile), through the
+    // cp.async ring with RING
+    float4 *ring = reinterpret_cast<float4 *>(
+        sh + hist_ring_offset_words(kKeysOnly ? 5 * size_t(G) : hist_smem_words(P, R, G)));
+    auto walk = [&](auto sd_tag, const int *box_lo, const int *len, int r0, int r1,
+                    const TileShape &ts, auto &&slot, auto &&quad) {
+        using SD = typename decltype(sd_tag)::type;
+        if constexpr (RING) {
+            walk_tile_async<D, kHistQmax, kHistStages, NoRow, SD>(in, stride, box_lo, len, r0, r1, ts,
+                                                                  ring, slot, no_row, quad);
+        } else {
+            walk_tile<D, kHistQmax, 4, NoRow, SD, false>(in, nullptr, stride, box_lo, len, r0, r1, ts,
+                                                         false, slot, no_row, quad);
+        }
+    };
+
     // ---- phase 1 (adaptive range only): min/max of every kernel of the group
-    if (ADAPTIVE) {
+    if (ADAPTIVE && MODE != kHistFlat) {
         auto key_min = [&](int kg, float v) { atomicMax(&s_keys[2 * kg], ~float_key(v)); };
         auto key_max = [&](int kg, float v) { atomicMax(&s_keys[2 * kg + 1], float_key(v)); };
         auto slow_elem = [&](int x, float v) {
@@ -473,14 +580,28 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                         }
                     }
                 };
-                walk_tile<D, kHistQmax, 4, NoRow, MSlot, false>(in, nullptr, stride, box_lo, len, r0, r1,
-                                                                ts, false, slot, no_row, quad);
+                walk(Tag<MSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
+                // warp-aggregated: one pair of shared atomics per warp and
+                // target kernel (256 threads' atomics on one key serialise)
 #pragma unroll
-                for (int i = 0; i < kHistQmax; ++i)
-                    if (tk[i] >= 0 && mn[i] <= mx[i]) {
-                        key_min(tk[i], mn[i]);
-                        key_max(tk[i], mx[i]);
+                for (int i = 0; i < kHistQmax; ++i) {
+                    const bool has = tk[i] >= 0 && mn[i] <= mx[i];
+                    const uint32_t kmn = has ? ~float_key(mn[i]) : 0u;
+                    const uint32_t kmx = has ? float_key(mx[i]) : 0u;
+                    unsigned pend = __ballot_sync(0xffffffffu, has);
+                    while (pend) {
+                        const int leader = __ffs(pend) - 1;
+                        const int t = __shfl_sync(0xffffffffu, tk[i], leader);
+                        const bool mine = has && tk[i] == t;
+                        pend &= ~__ballot_sync(0xffffffffu, mine);
+                        const uint32_t a = __reduce_max_sync(0xffffffffu, mine ? kmn : 0u);
+                        const uint32_t b = __reduce_max_sync(0xffffffffu, mine ? kmx : 0u);
+                        if (lane == leader) {
+                            atomicMax(&s_keys[2 * t], a);
+                            atomicMax(&s_keys[2 * t + 1], b);
+                        }
                     }
+                }
             } else {
                 // rows at varying alignments: voxel by voxel
                 for_voxels(box_lo, len, r0, r1, [&](int x, float v) {
@@ -493,6 +614,14 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                 });
             }
         });
+        if (MODE == kHistMinMax) {
+            __syncthreads();
+            for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
+                atomicMax(&kkeys[2 * (kfirst + kg)], s_keys[2 * kg]);
+                atomicMax(&kkeys[2 * (kfirst + kg) + 1], s_keys[2 * kg + 1]);
+            }
+            return;
+        }
         csync();   // every CTA's keys are complete
         for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
             uint32_t a = 0, b = 0;
@@ -503,6 +632,14 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
             }
             float lo, hi;
             keys_to_range(a, b, lo, hi);
+            s_lo[kg] = lo;
+            s_nlo[kg] = -lo;
+            s_sc[kg] = range_scale(lo, hi, nb);
+        }
+    } else if (ADAPTIVE) {   // flat pass: the range pass left the per-kernel keys
+        for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
+            float lo, hi;
+            keys_to_range(__ldcg(kkeys + 2 * (kfirst + kg)), __ldcg(kkeys + 2 * (kfirst + kg) + 1), lo, hi);
             s_lo[kg] = lo;
             s_nlo[kg] = -lo;
             s_sc[kg] = range_scale(lo, hi, nb);
@@ -570,8 +707,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                             if (sd.q0 + e >= 0 && sd.q0 + e < L) red_shared_add(bits[e] * r4 + base, wu);
                     }
                 };
-                walk_tile<D, kHistQmax, 4, NoRow, FSlot, false>(in, nullptr, stride, box_lo, len, r0, r1,
-                                                                ts, false, slot, no_row, quad);
+                walk(Tag<FSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
             } else if (tiled) {
                 // groups of kernels: a slot's quad goes to one kernel (with
                 // one multiplicity) when its first and last voxel do -- the
@@ -615,8 +751,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                             if (sd.q0 + e >= 0 && sd.q0 + e < L) add_elem(xs + sd.q0 + e, vals[e], wu);
                     }
                 };
-                walk_tile<D, kHistQmax, 4, NoRow, HSlot, false>(in, nullptr, stride, box_lo, len, r0, r1,
-                                                                ts, false, slot, no_row, quad);
+                walk(Tag<HSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
             } else {
                 // rows at varying alignments: voxel by voxel
                 for_voxels(box_lo, len, r0, r1, [&](int x, float v) {
@@ -646,31 +781,64 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         const int kg = t / (P - nb), j = nb + t % (P - nb);
         atomicAdd(&cnt[kg * P + nb - 1], cnt[kg * P + j]);
     }
+    if (MODE == kHistFlat) {
+        __syncthreads();
+        // add this CTA's counts to the item's global histograms
+        for (int t = threadIdx.x; t < GK * nb; t += blockDim.x) {
+            const int kg = t / nb, j = t - kg * nb;
+            const uint32_t c = cnt[size_t(kg) * P + j];
+            if (c) atomicAdd(&hist[(kfirst + kg) * nb + j], c);
+        }
+        __threadfence();   // every thread's counts before the ticket
+        __syncthreads();
+        __shared__ int s_last;
+        if (threadIdx.x == 0) {
+            const uint32_t done = uint32_t(c1 - c0);   // shares of this item done here
+            s_last = (atomicAdd(&tickets[item], done) + done == uint32_t(nchunks));
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        // the last contributor: every share's counts are in the global histograms
+        for (int t = threadIdx.x; t < GK * nb; t += blockDim.x) {
+            const int kg = t / nb, j = t - kg * nb;
+            cnt[size_t(kg) * P + j] = __ldcg(hist + (kfirst + kg) * nb + j);
+        }
+        for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
+            lo_out[kfirst + kg] = s_lo[kg];
+            scale_out[kfirst + kg] = s_sc[kg];
+        }
+        __syncthreads();
+        build_luts(cnt, P, GK, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut, kfirst, 1);
+        return;
+    }
     csync();   // every CTA's counts are complete
 
     // ---- phase 4: rank r owns kernels r, r + C, ...: sums the CTAs' counts
-    // in rank order, stores the histogram, builds the mapping table
-    for (int kg = rank; kg < GK; kg += C) {
-        uint32_t *ck = cnt + size_t(kg) * P;
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-            uint32_t s = 0;
-            if (C > 1) {
-                for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
-            } else {
-                s = ck[j];
-            }
-            ck[j] = s;
+    // in rank order into the copy area (free now), stores the histograms and
+    // ranges, builds the mapping tables
+    const int n_own = GK > rank ? (GK - rank + C - 1) / C : 0;
+    uint32_t *own = sh;   // [n_own][P]
+    for (int t = threadIdx.x; t < n_own * nb; t += blockDim.x) {
+        const int i = t / nb, j = t - i * nb;
+        const int kg = rank + i * C;
+        uint32_t s = 0;
+        if (C > 1) {
+            for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
+        } else {
+            s = cnt[size_t(kg) * P + j];
         }
-        __syncthreads();
-        const int64_t k = kfirst + kg;
-        uint32_t *gh = hist + k * nb;
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) gh[j] = ck[j];
-        block_lut(ck, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut + k * g.LS);
-        if (threadIdx.x == 0) {
-            lo_out[k] = s_lo[kg];
-            scale_out[k] = s_sc[kg];
-        }
+        own[size_t(i) * P + j] = s;
+        hist[(kfirst + kg) * nb + j] = s;
     }
+    for (int i = threadIdx.x; i < n_own; i += blockDim.x) {
+        const int kg = rank + i * C;
+        lo_out[kfirst + kg] = s_lo[kg];
+        scale_out[kfirst + kg] = s_sc[kg];
+    }
+    __syncthreads();
+    if (n_own > 0)
+        build_luts(own, P, n_own, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut, kfirst + rank, C);
     csync();   // the other CTAs' shared memory is no longer read
 }
 

@@ -1,6 +1,9 @@
 // k_map.cu -- launcher of the mapping pass of one volume: one CTA per chunk of
 // an inter-kernel cell (Sec. III.C, Eq. (12)-(13); the work of a CTA is in
 // map_impl.cuh).
+#include <algorithm>
+#include <cuda.h>
+
 #include "map_impl.cuh"
 
 namespace mclahe {
@@ -17,8 +20,109 @@ __global__ void __launch_bounds__(256, D >= 4 ? (ADAPTIVE ? 1 : 2) : (ADAPTIVE &
     map_cell<D, ADAPTIVE, REPL>(g, in, out, lut, lo_k, scale_k, cell, chunk, chunks, tab);
 }
 
+// TMA tiles (kWalkTma): the whole cell row along the last dim, as many rows
+// along dims D-2 and (4-D) 1 as fit in kTmaTileFloats, dividing the kernel
+// size so interior cells split into whole tiles.
+template <int D, bool ADAPTIVE>
+__global__ void __launch_bounds__(256, D >= 4 ? (ADAPTIVE ? 1 : 2) : 2)
+    k_map_tma(Geom g, const __grid_constant__ CUtensorMap tm_in,
+              const __grid_constant__ CUtensorMap tm_out, const float *__restrict__ in,
+              float *__restrict__ out, const float *__restrict__ lut,
+              const float *__restrict__ lo_k, const float *__restrict__ scale_k, int chunks, int bx,
+              int by, int bz, uint32_t *status) {
+    extern __shared__ __align__(128) float tab[];
+    const MapTma t{&tm_in, &tm_out, bx, by, bz, status};
+    const int64_t cell = blockIdx.x / chunks;
+    const int chunk = int(blockIdx.x - cell * chunks);
+    map_cell<D, ADAPTIVE, true, kWalkTma>(g, in, out, lut, lo_k, scale_k, cell, chunk, chunks, tab, &t);
+}
+
 bool map_replicated(const Geom &g) { return map_repl_fits(g.P); }
 size_t map_smem_bytes(const Geom &g) { return map_smem_for(g.D, g.P); }
+
+static int largest_divisor_at_most(int n, int cap) {
+    for (int d = std::min(n, cap); d > 1; --d)
+        if (n % d == 0) return d;
+    return 1;
+}
+
+// Whether the TMA walk applies (3- and 4-D, replicated tables, every cell
+// row starting on a 16-byte boundary, rows of 16-byte multiples), and its box.
+bool map_tma_box(const Geom &g, int &bx, int &by, int &bz) {
+    if (g.D < 3 || !map_repl_fits(g.P)) return false;
+    const Dim &dl = g.d[g.D - 1];
+    if (dl.s % 4 != 0 || dl.b % 4 != 0 || dl.b > 256) return false;
+    for (int c = 0; c + 1 < dl.n; ++c) {
+        const int lo = std::min(std::max(c * dl.b + dl.b / 2 - dl.p0, 0), dl.s);
+        if (lo % 4 != 0) return false;
+    }
+    bx = dl.b;
+    by = largest_divisor_at_most(g.d[g.D - 2].b, std::min(256, kTmaTileFloats / bx));
+    bz = g.D == 4 ? largest_divisor_at_most(g.d[1].b, std::min(256, kTmaTileFloats / (bx * by))) : 1;
+    return true;
+}
+
+static size_t map_tma_smem(const Geom &g) {
+    return map_table_bytes(g.D, g.P) + 128 + size_t(kTmaStages) * kTmaTileFloats * sizeof(float);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, through the runtime (no link to libcuda).
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of a volume (float32, dims innermost first) with the tile box.
+static cudaError_t encode_volume(CUtensorMap *m, const float *ptr, const Geom &g, int bx, int by,
+                                 int bz) {
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const int D = g.D;
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+    for (int i = 0; i < D; ++i) dims[i] = cuuint64_t(g.d[D - 1 - i].s);
+    for (int i = 1; i < D; ++i) strides[i - 1] = cuuint64_t(g.d[D - 1 - i].stride) * sizeof(float);
+    box[0] = cuuint32_t(bx);
+    box[1] = cuuint32_t(by);
+    box[2] = D == 4 ? cuuint32_t(bz) : 1u;
+    box[3] = 1u;
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, cuuint32_t(D),
+                           const_cast<float *>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int D, bool A>
+static cudaError_t launch_map_tma_t(const mclahe_plan_s &p, const float *in, float *out,
+                                    const unsigned char *ws, cudaStream_t st, unsigned grid, int bx,
+                                    int by, int bz) {
+    const size_t smem = map_tma_smem(p.g);
+    CUtensorMap m_in, m_out;
+    cudaError_t e = encode_volume(&m_in, in, p.g, bx, by, bz);
+    if (e == cudaSuccess) e = encode_volume(&m_out, out, p.g, bx, by, bz);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_map_tma<D, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_map_tma<D, A><<<grid, 256, smem, st>>>(
+        p.g, m_in, m_out, in, out, reinterpret_cast<const float *>(ws + p.ws.lut),
+        reinterpret_cast<const float *>(ws + p.ws.lo), reinterpret_cast<const float *>(ws + p.ws.scale),
+        p.t.map_chunks, bx, by, bz, reinterpret_cast<uint32_t *>(const_cast<unsigned char *>(ws) + p.ws.status));
+    return cudaGetLastError();
+}
 
 template <int D, bool A, bool REPL>
 static cudaError_t launch_map_t(const mclahe_plan_s &p, const float *in, float *out,
@@ -39,6 +143,13 @@ static cudaError_t launch_map_d(const mclahe_plan_s &p, const float *in, float *
                                 const unsigned char *ws, cudaStream_t st) {
     const Geom &g = p.g;
     const unsigned grid = unsigned(n_cells(g) * p.t.map_chunks);
+    int bx, by, bz;
+    if constexpr (D >= 3) {
+        if (p.t.map_tma && map_tma_box(g, bx, by, bz))
+            return g.mode == MCLAHE_RANGE_ADAPTIVE
+                       ? launch_map_tma_t<D, true>(p, in, out, ws, st, grid, bx, by, bz)
+                       : launch_map_tma_t<D, false>(p, in, out, ws, st, grid, bx, by, bz);
+    }
     const size_t smem = map_smem_bytes(g);
     const bool repl = map_replicated(g);
     if (g.mode == MCLAHE_RANGE_ADAPTIVE)

@@ -38,8 +38,33 @@
 #pragma once
 
 #include "mclahe_internal.cuh"
+#include "tma.cuh"
 
 namespace mclahe {
+
+// How a CTA streams its cell's voxels:
+//   kWalkLsu   fixed quad slots with 128-bit loads (walk_tile);
+//   kWalkRing  the same slots through a cp.async row ring (walk_tile_async);
+//   kWalkTma   box tiles of the cell through TMA: a ring of kTmaStages tiles
+//              in shared memory, loaded by one thread with cp.async.bulk.tensor
+//              and completed on mbarriers; each thread maps its quads of a
+//              tile in place and one thread stores the tile back with a TMA
+//              store.  Cells whose rows are short (a few sectors of a 128-byte
+//              line) cost the load/store unit a wavefront per line per request
+//              in the other walks; TMA moves whole boxes instead.
+constexpr int kWalkLsu = 0, kWalkRing = 1, kWalkTma = 2;
+constexpr int kTmaStages = 4;
+constexpr int kTmaTileFloats = 2048;   // at most; 2 quads per thread of 256
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
+
+// The tile box and tensor maps of a TMA mapping launch.  The box spans the
+// whole cell row (bx = b of the last dim), by voxels along dim D-2, bz along
+// dim D-3 (4-D only) and one slice along dim 0; tiles step along dim 0 first.
+struct MapTma {
+    const CUtensorMap *in, *out;
+    int bx, by, bz;
+    uint32_t *status;   // workspace status word (a wait that gave up)
+};
 
 // Rotate an array of N values left by r (0 <= r < N, N a power of two) with
 // log2(N) levels of selects, keeping every index static.
@@ -73,12 +98,13 @@ __host__ __device__ inline size_t map_smem_for(int D, int P, bool ring = true) {
 
 __device__ __forceinline__ void sts128(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-template <int D, bool ADAPTIVE, bool REPL, bool RING = true>
+template <int D, bool ADAPTIVE, bool REPL, int WALK = kWalkRing>
 __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict__ in,
                                          float *__restrict__ out, const float *__restrict__ lut,
                                          const float *__restrict__ lo_k,
                                          const float *__restrict__ scale_k, int64_t cell, int chunk,
-                                         int chunks, float *tab) {
+                                         int chunks, float *tab, const MapTma *tma = nullptr) {
+    constexpr bool RING = WALK == kWalkRing;
     constexpr int NC = 1 << D;          // corners
     constexpr int NO = 1 << (D - 1);    // corners over dims 0..D-2
     constexpr int NQ = NC >= 4 ? NC / 4 : 1;   // 16-byte corner quads per index
@@ -335,6 +361,132 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                 if (e0 + e >= 0 && e0 + e < L) out[a + e] = res[e];
         }
     };
+
+    if constexpr (WALK == kWalkTma) {
+        static_assert(D >= 3 && REPL, "TMA tiles: 3- and 4-D cells, replicated tables");
+        constexpr int NS = kTmaStages;
+        constexpr int QT = kTmaTileFloats / 4 / 256;   // quad slots per thread
+        constexpr int R = D;                           // box rank
+        const int Bx = tma->bx, By = tma->by, Bz = D == 4 ? tma->bz : 1;
+        const int tile_q = (Bx * By * Bz) >> 2;
+        const uint32_t tile_bytes = uint32_t(Bx * By * Bz) * 4u;
+        constexpr uint32_t kStageBytes = kTmaTileFloats * 4;
+        __shared__ __align__(8) uint64_t s_bar[NS];
+        const uint32_t bar0 = uint32_t(__cvta_generic_to_shared(s_bar));
+        const uint32_t stage0 = (tab_s + uint32_t(map_table_bytes(D, P)) + 127u) & ~127u;
+        // tiles of this cell: slices along dim 0 innermost, then blocks along
+        // dim D-2, then (4-D) along dim 1; this CTA takes a contiguous range
+        const int ny = (len[D - 2] + By - 1) / By;
+        const int nz = D == 4 ? (len[1] + Bz - 1) / Bz : 1;
+        const int n0 = len[0];
+        const int nt_all = n0 * ny * nz;
+        const int kb = int((int64_t(nt_all) * chunk) / chunks);
+        const int nt = int((int64_t(nt_all) * (chunk + 1)) / chunks) - kb;
+        struct Tile {
+            int c[R];     // box origin, innermost first
+            bool full;    // the box lies inside the cell (TMA store)
+        };
+        auto tile = [&](int k) {
+            Tile t;
+            const int kk = kb + k;
+            const int sl = kk % n0, blk = kk / n0;
+            const int yb = blk % ny, zb = blk / ny;
+            t.c[0] = box_lo[D - 1];
+            t.c[1] = box_lo[D - 2] + yb * By;
+            if (D == 4) t.c[2] = box_lo[1] + zb * Bz;
+            t.c[R - 1] = box_lo[0] + sl;
+            t.full = len[D - 1] == Bx && (yb + 1) * By <= len[D - 2] &&
+                     (D < 4 || (zb + 1) * Bz <= len[1]);
+            return t;
+        };
+        auto issue = [&](int k) {
+            const Tile t = tile(k);
+            const uint32_t bar = bar0 + 8u * uint32_t(k % NS);
+            mbar_expect_tx(bar, tile_bytes);
+            tma_load<R>(stage0 + uint32_t(k % NS) * kStageBytes, tma->in, t.c, bar);
+        };
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) mbar_init(bar0 + 8u * i, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < NS - 1 && k < nt; ++k) issue(k);
+        // this thread's quads of a tile: in-tile coordinates (fixed)
+        int qx[QT], qy[QT], qz[QT];
+        bool qv[QT];
+#pragma unroll
+        for (int i = 0; i < QT; ++i) {
+            const int qi = int(threadIdx.x) + i * int(blockDim.x);
+            qv[i] = qi < tile_q;
+            const int e = 4 * qi;
+            qx[i] = e % Bx;
+            const int rest = e / Bx;
+            qy[i] = rest % By;
+            qz[i] = rest / By;
+        }
+        const int lx = len[D - 1];
+        for (int k = 0; k < nt; ++k) {
+            const int stg = k % NS;
+            if (!mbar_wait_bounded(bar0 + 8u * uint32_t(stg), uint32_t(k / NS) & 1u, kTmaWaitLimit) &&
+                tma->status)
+                atomicCAS(tma->status, 0u, uint32_t(MCLAHE_ERR_TIMEOUT));
+            const Tile t = tile(k);
+            const uint32_t sbase = stage0 + uint32_t(stg) * kStageBytes;
+#pragma unroll
+            for (int i = 0; i < QT; ++i) {
+                if (!qv[i]) continue;
+                // absolute voxel coordinates of the quad
+                const int x = t.c[0] + qx[i], y = t.c[1] + qy[i];
+                const int z = D == 4 ? t.c[2] + qz[i] : 0;
+                const bool in_cell = qx[i] < lx && y < box_lo[D - 2] + len[D - 2] &&
+                                     (D < 4 || z < box_lo[1] + len[1]);
+                if (!in_cell) continue;
+                const uint32_t qa = sbase + 16u * uint32_t(int(threadIdx.x) + i * int(blockDim.x));
+                const float4 v = lds128(qa);
+                int coords[kMaxDim];
+                coords[0] = t.c[R - 1];
+                if (D == 4) {
+                    coords[1] = z;
+                    coords[2] = y;
+                } else {
+                    coords[1] = y;
+                }
+                MRow st;
+                row_fn(coords, 0, st);
+                const float vals[4] = {v.x, v.y, v.z, v.w};
+                float res[4];
+                map4(st, vals, float(2 * x + mb_l) * inv2b_l, res);
+                if (t.full) {
+                    // in place: the tile goes back with one TMA store
+                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(qa), "f"(res[0]),
+                                 "f"(res[1]), "f"(res[2]), "f"(res[3])
+                                 : "memory");
+                } else {
+                    int64_t a = x;
+#pragma unroll
+                    for (int j = 0; j < D - 1; ++j) a += int64_t(coords[j]) * stride[j];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (qx[i] + e < lx) out[a + e] = res[e];
+                }
+            }
+            if (t.full) fence_proxy_async_smem();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (t.full) tma_store<R>(tma->out, t.c, sbase);
+                bulk_commit();
+                const int kn = k + NS - 1;
+                if (kn < nt) {
+                    bulk_wait_read<1>();   // the store of tile k - 1 has read its stage
+                    issue(kn);
+                }
+            }
+        }
+        if (threadIdx.x == 0) bulk_wait_all();
+        return;
+    }
 
     if ((g.d[D - 1].s & 3) == 0) {
         // every row starts at the same alignment: fixed quad slots per thread

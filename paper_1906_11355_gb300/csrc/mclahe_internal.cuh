@@ -75,15 +75,18 @@ struct Tuning {
     int hist_chunks;    // CTAs per kernel (cluster size) in the histogram pass
     int hist_copies;    // lane copies of the shared-memory histograms (1 .. 32)
     int hist_group;     // kernels along the last dimension per histogram work item
+    int hist_shares;    // shares per work item in the flat histogram pass (0: one
+                        // cluster of hist_chunks CTAs per work item)
     int map_threads;    // threads per mapping CTA
     int map_chunks;     // CTAs per inter-kernel cell in the mapping pass
+    int map_tma;        // 1: stream 3- and 4-D cells as TMA tiles (where map_tma_box allows)
     int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)
 };
 
 // Workspace layout (byte offsets, kWsAlign aligned).
 struct Layout {
-    size_t status, keys, hist, lo, scale, lut, scratch, total;
-    size_t keys_count;  // uint32 range keys (2: the global range)
+    size_t status, keys, tickets, hist, lo, scale, lut, scratch, total;
+    size_t keys_count;  // uint32 range keys: the global range, then one pair per kernel
     size_t scratch_bytes;
 };
 
@@ -95,6 +98,7 @@ struct mclahe_plan_s {
     mclahe::Layout ws;
     int64_t pad[mclahe::kMaxDim];
     int tuned;          // launch shapes come from mclahe_autotune
+    mutable int flat_ctas = 0;   // grid of the last flat histogram launch
 };
 
 namespace mclahe {
@@ -486,6 +490,12 @@ __device__ __forceinline__ void walk_box(const float *__restrict__ in,
 // loads are issued before the current row is consumed.  QL <= QMAX is required: boxes with rows longer
 // than 4 * 32 * QMAX - 3 elements must be split along the last dimension.
 // ---------------------------------------------------------------------------
+// A type carried as a value (to name a local type in a generic lambda).
+template <typename T>
+struct Tag {
+    using type = T;
+};
+
 struct TileShape {
     int head;   // first row element's offset in its aligned quad
     int Q;      // quads per row
@@ -732,9 +742,14 @@ cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float
                             unsigned char *ws, const float *d_clip, float *d_grad_lut,
                             float *d_grad_clip, cudaStream_t st);
 size_t bwd_partial_floats(const Geom &g, int chunks);
-size_t hist_smem_bytes(const Geom &g, int copies, int group);
+// Dynamic shared memory of a histogram CTA (with the row ring of the
+// per-volume launches, without it in the batched launch).
+size_t hist_smem_bytes(const Geom &g, int copies, int group, bool ring = true);
+cudaError_t launch_hist_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+                              cudaStream_t st);
 int64_t hist_items(const Geom &g, int group);
 size_t map_smem_bytes(const Geom &g);
+bool map_tma_box(const Geom &g, int &bx, int &by, int &bz);
 bool map_replicated(const Geom &g);
 
 // batch.cu

@@ -53,10 +53,10 @@ Tuning default_tuning(const Geom &g) {
     const Dim &dl = g.d[g.D - 1];
     int G = std::min(dl.n, std::max(1, (64 + dl.b - 1) / dl.b));
     int R = 16;
-    while (R > 1 && (hist_smem_bytes(g, R, G) > 64 * 1024 ||
+    while (R > 1 && (hist_smem_bytes(g, R, G, false) > 64 * 1024 ||
                      int64_t(g.P) * R * G > std::max<int64_t>(g.V * G / 2, int64_t(g.P) * G)))
         R >>= 1;
-    while (G > 1 && hist_smem_bytes(g, R, G) > 100 * 1024) G >>= 1;
+    while (G > 1 && hist_smem_bytes(g, R, G, false) > 100 * 1024) G >>= 1;
     t.hist_group = G;
     t.hist_copies = R;
     const int sms = 152;
@@ -68,6 +68,11 @@ Tuning default_tuning(const Geom &g) {
                      (items * C < sms && vitem / (2 * C) >= 16 * 1024)))
         C <<= 1;
     t.hist_chunks = C;
+    // flat form: about 16 shares per CTA of one wave (the launch bounds' CTAs
+    // per SM), so the CTAs' work differs by at most about 1/16
+    const int64_t wave = int64_t(sms) * (g.D >= 4 ? 2 : 3);
+    const int64_t item_rows = std::max<int64_t>(g.V / dl.b, 1);
+    t.hist_shares = int(std::min<int64_t>(std::min<int64_t>((16 * wave + items - 1) / items, 256), item_rows));
     int64_t rows = 1, cell_vox = dl.b;   // rows and voxels of an interior cell
     for (int j = 0; j + 1 < g.D; ++j) {
         rows *= g.d[j].b;
@@ -77,6 +82,10 @@ Tuning default_tuning(const Geom &g) {
     int64_t mc = (cell_vox + 65535) / 65536;
     while (cells * mc < sms && cell_vox / (mc + 1) >= 8 * 1024) ++mc;
     t.map_chunks = int(std::min<int64_t>(std::max<int64_t>(std::min(mc, rows), 1), 64));
+    // TMA tiles for cell rows shorter than a 128-byte line, where per-thread
+    // requests would touch a line per 32 bytes
+    int bx, by, bz;
+    t.map_tma = (map_tma_box(g, bx, by, bz) && dl.b < 32) ? 1 : 0;
     int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
     t.bwd_chunks = int(std::min<int64_t>(bc, 32));
@@ -88,9 +97,12 @@ Layout make_layout(const Geom &g, const Tuning &t) {
     size_t off = 0;
     L.status = off;
     off = align_up(off + sizeof(uint32_t) * 4);
-    L.keys_count = 2;
+    // range keys, work-item tickets and histograms are adjacent: the flat
+    // histogram pass accumulates all three and clears them with one memset
+    L.keys_count = 2 + 2 * size_t(g.K);
     L.keys = off;
-    off = align_up(off + sizeof(uint32_t) * L.keys_count);
+    L.tickets = off + sizeof(uint32_t) * L.keys_count;
+    off = align_up(L.tickets + sizeof(uint32_t) * size_t(g.K));
     L.hist = off;
     off = align_up(off + sizeof(uint32_t) * size_t(g.K) * g.nb);
     L.lo = off;
@@ -124,11 +136,19 @@ mclahe_status run_pass(const mclahe_plan_s &p, int pass, const float *in, float 
     cudaError_t e = cudaSuccess;
     switch (pass) {
         case MCLAHE_PASS_CLEAR:
-            // only the global range keys are accumulated with atomics
-            if (p.g.mode == MCLAHE_RANGE_GLOBAL && !p.g.has_range)
+            // what later passes accumulate with atomics: the range keys, and
+            // in the flat histogram pass the tickets and histograms
+            if (p.t.hist_shares > 0)
+                e = cudaMemsetAsync(ws + p.ws.keys, 0,
+                                    p.ws.hist + sizeof(uint32_t) * size_t(p.g.K) * p.g.nb - p.ws.keys, st);
+            else if (p.g.mode == MCLAHE_RANGE_GLOBAL && !p.g.has_range)
                 e = cudaMemsetAsync(ws + p.ws.keys, 0, 2 * sizeof(uint32_t), st);
             break;
-        case MCLAHE_PASS_RANGE: e = launch_range(p, in, ws, st); break;
+        case MCLAHE_PASS_RANGE:
+            e = p.g.mode == MCLAHE_RANGE_ADAPTIVE && p.t.hist_shares > 0
+                    ? launch_hist_range(p, in, ws, st)
+                    : launch_range(p, in, ws, st);
+            break;
         case MCLAHE_PASS_HIST: e = launch_hist(p, in, ws, d_clip, st); break;
         case MCLAHE_PASS_LUT: break;   // built by the histogram pass's clusters
         case MCLAHE_PASS_MAP: e = launch_map(p, in, out, ws, st); break;
@@ -266,11 +286,38 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->ws_scratch = p->ws.scratch;
     info->ws_bytes = p->ws.total;
     info->hist_group = p->t.hist_group;
-    info->hist_cluster = p->t.hist_chunks;
+    info->hist_cluster = p->t.hist_shares > 0 ? 1 : p->t.hist_chunks;
+    info->hist_shares = p->t.hist_shares;
+    info->hist_ctas = p->t.hist_shares > 0 ? p->flat_ctas : 0;
+    info->map_tma = p->t.map_tma;
     info->hist_copies = p->t.hist_copies;
     info->map_chunks = p->t.map_chunks;
     info->bwd_chunks = p->t.bwd_chunks;
     info->tuned = p->tuned;
+    return MCLAHE_OK;
+}
+
+mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_t hist_cluster,
+                                     int32_t hist_copies, int32_t hist_shares, int32_t map_chunks,
+                                     int32_t map_tma) {
+    if (!p) return MCLAHE_ERR_INVALID_ARG;
+    auto pow2 = [](int32_t v, int32_t hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
+    const Geom &g = p->g;
+    if (hist_group < 1 || hist_group > g.d[g.D - 1].n) return MCLAHE_ERR_INVALID_ARG;
+    if (!pow2(hist_cluster, 8) || !pow2(hist_copies, 32)) return MCLAHE_ERR_INVALID_ARG;
+    if (hist_shares < 0 || hist_shares > 4096 || (hist_shares > 0 && hist_cluster != 1))
+        return MCLAHE_ERR_INVALID_ARG;
+    if (map_chunks < 1 || map_chunks > 64) return MCLAHE_ERR_INVALID_ARG;
+    int bx, by, bz;
+    if (map_tma != 0 && (map_tma != 1 || !map_tma_box(g, bx, by, bz))) return MCLAHE_ERR_INVALID_ARG;
+    if (hist_smem_bytes(g, hist_copies, hist_group) > 220 * 1024) return MCLAHE_ERR_INVALID_ARG;
+    p->t.hist_group = hist_group;
+    p->t.hist_chunks = hist_cluster;
+    p->t.hist_copies = hist_copies;
+    p->t.hist_shares = hist_shares;
+    p->t.map_chunks = map_chunks;
+    p->t.map_tma = map_tma;
+    p->tuned = 2;
     return MCLAHE_OK;
 }
 
@@ -306,7 +353,8 @@ int mclahe_pass_launches(mclahe_plan_t p, mclahe_pass pass) {
     if (!p) return 0;
     switch (pass) {
         case MCLAHE_PASS_RANGE:
-            return (p->g.mode == MCLAHE_RANGE_GLOBAL && !p->g.has_range) ? 1 : 0;
+            if (p->g.mode == MCLAHE_RANGE_ADAPTIVE) return p->t.hist_shares > 0 ? 1 : 0;
+            return p->g.has_range ? 0 : 1;
         case MCLAHE_PASS_HIST:
         case MCLAHE_PASS_MAP: return 1;
         default: return 0;

@@ -100,3 +100,36 @@ def test_forward_rejects_bad_pointers_without_touching_the_device(nat):
     assert lib.mclahe_forward(plan.handle, 4096, 8192, 16384, ws - 1, None, None) == nat.MCLAHE_ERR_WORKSPACE
     assert lib.mclahe_forward(plan.handle, 4096, 8192, 16400, ws, None, None) == nat.MCLAHE_ERR_WORKSPACE
     assert lib.mclahe_forward(None, 4096, 8192, 16384, ws, None, None) == nat.MCLAHE_ERR_INVALID_ARG
+
+
+def test_set_shapes_validates_and_round_trips(nat):
+    plan = nat.mclahe_plan((64, 512, 512), (16, 64, 64), 256, 0.02, nat.MCLAHE_RANGE_ADAPTIVE)
+    n_last = nat.mclahe_plan_query(plan)["n_kernels_dim"][-1]
+    nat.mclahe_plan_set_shapes(plan, 2, 1, 8, 24, 3)
+    info = nat.mclahe_plan_query(plan)
+    assert (info["hist_group"], info["hist_cluster"], info["hist_copies"], info["hist_shares"],
+            info["map_chunks"], info["tuned"]) == (2, 1, 8, 24, 3, 2)
+    # the adaptive range gets a flat range pass of its own in the flat form
+    assert nat.mclahe_pass_launches(plan, nat.MCLAHE_PASS_RANGE) == 1
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1)
+    assert nat.mclahe_plan_query(plan)["hist_shares"] == 0
+    assert nat.mclahe_pass_launches(plan, nat.MCLAHE_PASS_RANGE) == 0
+    bad = [(0, 1, 8, 0, 1), (n_last + 1, 1, 8, 0, 1), (1, 3, 8, 0, 1), (1, 16, 8, 0, 1),
+           (1, 1, 12, 0, 1), (1, 1, 64, 0, 1), (1, 2, 8, 4, 1), (1, 1, 8, -1, 1),
+           (1, 1, 8, 4097, 1), (1, 1, 8, 0, 0), (1, 1, 8, 0, 65)]
+    for args in bad:
+        with pytest.raises(nat.MclaheError) as e:
+            nat.mclahe_plan_set_shapes(plan, *args)
+        assert e.value.status == nat.MCLAHE_ERR_INVALID_ARG, args
+    # TMA tiles: this geometry's cell rows start on 16-byte boundaries
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 1)
+    assert nat.mclahe_plan_query(plan)["map_tma"] == 1
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0)
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 2)
+    odd = nat.mclahe_plan((19, 23, 29), (5, 4, 7), 100, 0.02)
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 1)
+    info = nat.mclahe_plan_query(plan)   # unchanged by the rejected calls
+    assert (info["hist_group"], info["hist_cluster"], info["hist_copies"], info["hist_shares"],
+            info["map_chunks"]) == (1, 4, 16, 0, 1)

@@ -2,9 +2,12 @@
 kernel and cell tiles of many volumes, with per-volume ready counters) against
 the per-volume forward pass and the FP64 oracle.
 
-The batch runs the same per-kernel and per-cell code as mclahe_forward, so its
-histograms, tables and outputs must equal the per-volume results bit for bit,
-whatever the tile order; the oracle check keeps the usual 1e-5 bound."""
+The batch runs the same per-kernel and per-cell code as mclahe_forward with
+per-thread loads, so its histograms, tables and outputs must equal those
+per-volume results bit for bit, whatever the tile order.  (The corner sums of a
+voxel run in a lane-rotated order, so a walk that gives voxels to other lanes,
+such as the TMA tiles, may differ in the last bits.)  The oracle check keeps
+the usual 1e-5 bound."""
 import numpy as np
 import pytest
 
@@ -63,6 +66,7 @@ def test_batch_equals_per_volume_forward_and_oracle(torch_cuda, orc, use_graph):
     for x, xh, s, out in zip(xs, xs_h, specs, outs):
         op = MCLAHE(s["shape"], s["kernel"], s["n_bins"], s["clip_limit"], s["adaptive"],
                     s.get("global_range"))
+        op.set_shapes(**{**op.shapes(), "map_tma": 0})   # the batch's lane assignment
         ref = op.forward(x)
         torch.cuda.synchronize()
         assert torch.equal(out, ref), s

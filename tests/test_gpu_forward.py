@@ -28,12 +28,14 @@ def f32(c):
     return float(np.float32(c))
 
 
-def run_case(torch, orc, x, ks, nb, clip, adaptive=False, global_range=None):
+def run_case(torch, orc, x, ks, nb, clip, adaptive=False, global_range=None, shapes=None):
     from paper_1906_11355_gb300.api import MCLAHE
 
     clip = f32(clip)
     op = MCLAHE(x.shape, ks, n_bins=nb, clip_limit=clip, adaptive=adaptive,
                 global_range=global_range)
+    if shapes is not None:
+        op.set_shapes(**shapes)
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     out = op.forward(xd)
     torch.cuda.synchronize()
@@ -78,6 +80,86 @@ def test_forward_matches_oracle(torch_cuda, orc, case):
     rng = np.random.default_rng(hash((shape, ks, nb)) % 2**32)
     x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
     run_case(torch_cuda, orc, x, ks, nb, clip, adaptive)
+
+
+# both histogram forms with explicit launch shapes: clusters of 1-8 CTAs, and
+# the flat form with 1 share per item up to more shares than an item has rows
+FORM_CASES = [
+    ((53, 47), (8, 7), 64, 0.01, False),
+    ((19, 23, 29), (5, 4, 7), 100, 0.02, True),
+    ((16, 64, 64), (4, 16, 16), 256, 0.02, True),
+    ((11, 9, 13, 10), (3, 4, 5, 2), 50, 0.03, False),
+    ((11, 9, 13, 10), (3, 4, 5, 2), 50, 0.03, True),
+]
+FORMS = [dict(hist_group=1, hist_cluster=4, hist_copies=4, hist_shares=0, map_chunks=2),
+         dict(hist_group=1, hist_cluster=1, hist_copies=8, hist_shares=1, map_chunks=1),
+         dict(hist_group=2, hist_cluster=1, hist_copies=2, hist_shares=7, map_chunks=1),
+         dict(hist_group=1, hist_cluster=1, hist_copies=16, hist_shares=300, map_chunks=3)]
+
+
+@pytest.mark.parametrize("form", range(len(FORMS)))
+@pytest.mark.parametrize("case", FORM_CASES,
+                         ids=[str(c[0]) + ("A" if c[4] else "G") for c in FORM_CASES])
+def test_histogram_forms_match_oracle(torch_cuda, orc, case, form):
+    shape, ks, nb, clip, adaptive = case
+    rng = np.random.default_rng(hash((shape, ks, nb, form)) % 2**32)
+    x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
+    shapes = dict(FORMS[form])
+    # clusters of whole kernels: at most the kernels along the last dimension
+    from paper_1906_11355_gb300 import _native as nat
+
+    n_last = nat.mclahe_plan_query(nat.mclahe_plan(shape, ks, nb, f32(clip), int(adaptive)))[
+        "n_kernels_dim"][-1]
+    shapes["hist_group"] = min(shapes["hist_group"], n_last)
+    op, _, _ = run_case(torch_cuda, orc, x, ks, nb, clip, adaptive, shapes=shapes)
+    assert {k: v for k, v in op.shapes().items() if k in shapes} == shapes
+    # a second call on the same workspace (the flat form's accumulators are cleared)
+    x2 = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
+    xd = torch_cuda.from_numpy(x2).cuda()
+    got = op.forward(xd).cpu().numpy().astype(np.float64)
+    want = orc.mclahe(x2, ks, nb, f32(clip), mode=int(adaptive))
+    assert np.abs(got - want).max() <= OUT_TOL
+
+
+# the mapping pass on TMA box tiles: 3- and 4-D, both range modes, cells cut
+# into whole tiles and edge cells with partial tiles (per-element stores)
+TMA_CASES = [
+    ((12, 40, 64), (4, 8, 8), 64, 0.02, False),
+    ((20, 24, 48), (5, 6, 12), 128, 0.01, True),
+    ((6, 10, 12, 16), (3, 5, 4, 8), 512, 0.01, False),
+    ((8, 8, 16, 24), (4, 4, 8, 8), 100, 0.03, True),
+    ((13, 37, 36), (4, 6, 12), 256, 0.02, False),
+    ((9, 11, 14, 20), (3, 4, 5, 4), 50, 0.05, True),
+]
+
+
+@pytest.mark.parametrize("chunks", [1, 3])
+@pytest.mark.parametrize("case", TMA_CASES, ids=[str(c[0]) + ("A" if c[4] else "G") for c in TMA_CASES])
+def test_tma_mapping_matches_oracle(torch_cuda, orc, case, chunks):
+    from paper_1906_11355_gb300 import _native as nat
+
+    shape, ks, nb, clip, adaptive = case
+    rng = np.random.default_rng(hash((shape, ks, nb, chunks)) % 2**32)
+    x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
+    x[rng.random(size=shape) < 0.3] = 0.0   # many voxels in bin 0 (global range)
+    plan = nat.mclahe_plan(shape, ks, nb, f32(clip), int(adaptive))
+    shapes = {k: v for k, v in nat.mclahe_plan_query(plan).items()
+              if k in ("hist_group", "hist_cluster", "hist_copies", "hist_shares")}
+    shapes.update(map_chunks=chunks, map_tma=1)
+    op, out, _ = run_case(torch_cuda, orc, x, ks, nb, clip, adaptive, shapes=shapes)
+    assert op.shapes()["map_tma"] == 1
+    assert nat.mclahe_sync_status(op.ws) == 0
+
+
+def test_tma_mapping_rejected_where_rows_are_unaligned(torch_cuda):
+    from paper_1906_11355_gb300.api import MCLAHE
+    from paper_1906_11355_gb300 import _native as nat
+
+    op = MCLAHE((19, 23, 29), (5, 4, 7), n_bins=100, clip_limit=0.02)
+    sh = op.shapes()
+    sh["map_tma"] = 1
+    with pytest.raises(nat.MclaheError):
+        op.set_shapes(**sh)
 
 
 def test_given_global_range_and_out_of_range_values(torch_cuda, orc):

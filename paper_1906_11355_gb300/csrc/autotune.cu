@@ -5,7 +5,8 @@
 // last dimension x lane copies R in {2, 4, 8, 16, 32} (shared memory with the
 // row ring at most 200 KiB) x form: a cluster of C in {1, 2, 4, 8} CTAs per
 // item, or the flat form with S in {1, 2, 4, ..., 256} shares per item (with
-// its range pass, under the adaptive range).  Mapping pass: per-thread loads
+// its range pass, under the adaptive range) x row walk: the cp.async ring or
+// TMA tiles (where the geometry allows).  Mapping pass: per-thread loads
 // or TMA tiles (where the geometry allows) x CTAs per cell in {1, 2, 4, ...,
 // 64} (at most one row per CTA).  Each candidate runs twice
 // after one warm-up and keeps its faster time; results are cached per
@@ -109,13 +110,18 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
             p->t.hist_group = G;
             p->t.hist_copies = R;
             // cluster form: C CTAs per item; flat form: S shares per item
-            for (int v = 0; v < 4 + 9; ++v) {
-                if (v < 4) {
-                    p->t.hist_chunks = 1 << v;
+            int bx, by;
+            const int n_walks = hist_tma_box(p->g, G, bx, by) ? 2 : 1;
+            for (int v = 0; v < (4 + 9) * n_walks; ++v) {
+                const int f = v % 13;
+                p->t.hist_tma = v / 13;
+                if (p->t.hist_tma && hist_smem_bytes(p->g, R, G, 2) > 200 * 1024) continue;
+                if (f < 4) {
+                    p->t.hist_chunks = 1 << f;
                     p->t.hist_shares = 0;
                 } else {
                     p->t.hist_chunks = 1;
-                    p->t.hist_shares = 1 << (v - 4);
+                    p->t.hist_shares = 1 << (f - 4);
                     if (p->t.hist_shares > item_rows) continue;
                 }
                 const float ms = time_passes(*p, MCLAHE_PASS_CLEAR, MCLAHE_PASS_HIST, d_in, d_out,
@@ -127,6 +133,7 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
                     best.hist_chunks = p->t.hist_chunks;
                     best.hist_shares = p->t.hist_shares;
                     best.hist_copies = R;
+                    best.hist_tma = p->t.hist_tma;
                 }
             }
         }

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256, D <= 2 ? 3 : ((D >= 4 && ADAPTIVE) ? 1 : 
 template <int D, bool A>
 cudaError_t launch_batch_t(const BParams &bp, int C, size_t smem, cudaStream_t st) {
     auto kern = k_batch<D, A>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), size_t(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(256);

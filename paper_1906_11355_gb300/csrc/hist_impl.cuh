@@ -36,6 +36,7 @@
 #include <cooperative_groups.h>
 
 #include "mclahe_internal.cuh"
+#include "tma.cuh"
 
 namespace mclahe {
 
@@ -293,11 +294,28 @@ __device__ __forceinline__ void build_luts(const uint32_t *h, int P, int n, int 
 __host__ __device__ inline size_t hist_smem_words(int P, int R, int G) {
     return size_t(G) * P * R + size_t(G) * P + 5 * size_t(G);
 }
-// With RING, the rows of a box stream through a cp.async ring behind these
-// words (walk_tile_async: kHistStages row stages of kHistQmax quads per
-// thread), so two rows per thread are in flight while one is counted.
+// How a CTA streams the rows of a box (the shared memory behind these words):
+//   kHistLsu   walk_tile, 128-bit loads into registers (batched launch);
+//   kHistRing  walk_tile_async: a cp.async ring of kHistStages row stages of
+//              kHistQmax quads per thread, two rows per thread in flight;
+//   kHistTma   walk_tile_tma: box tiles of up to kHistTileFloats floats
+//              loaded by TMA into kHistTmaStages stages (boxes wider than the
+//              tile fall back to the ring).
+constexpr int kHistLsu = 0, kHistRing = 1, kHistTma = 2;
+// Boxes along the last dim are cut into segments of at most kHistSeg elements.
+constexpr int kHistSeg = 4 * 32 * 4 - 4;
 constexpr int kHistQmax = 4;     // quad slots per thread and row in the histogram pass
 constexpr int kHistStages = 3;
+constexpr int kHistTmaStages = 4;
+constexpr int kHistTileFloats = 2048;   // 2 quads per thread of 256
+constexpr uint32_t kHistTmaStage = kHistTileFloats * 4;
+
+// Tensor map of the volume with its tile box (Bx elements along the last dim,
+// By rows along dim D-2), for kHistTma.
+struct HistTma {
+    const CUtensorMap *map;
+    int bx, by;
+};
 __host__ __device__ inline size_t hist_ring_offset_words(size_t words) { return (words + 3) & ~size_t(3); }
 __host__ __device__ inline size_t hist_ring_bytes(int nthreads) {
     return size_t(kHistStages) * kHistQmax * size_t(nthreads) * 16;
@@ -363,7 +381,7 @@ __device__ __forceinline__ Targets last_targets(const Dim &d, int x, int kl0, in
 //                  per-kernel keys with atomic max.
 constexpr int kHistCluster = 0, kHistFlat = 1, kHistMinMax = 2;
 
-template <int D, bool ADAPTIVE, int MODE = kHistCluster, bool RING = false>
+template <int D, bool ADAPTIVE, int MODE = kHistCluster, int HW = kHistLsu>
 __device__ __forceinline__ void hist_group(const Geom &g, const float *__restrict__ in,
                                            const uint32_t *__restrict__ keys,
                                            const float *__restrict__ d_clip,
@@ -373,7 +391,9 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                                            int R, uint32_t *sh, int c0 = 0, int c1 = 1,
                                            int nchunks = 1,
                                            uint32_t *__restrict__ tickets = nullptr,
-                                           uint32_t *__restrict__ kkeys = nullptr) {
+                                           uint32_t *__restrict__ kkeys = nullptr,
+                                           const HistTma *htma = nullptr,
+                                           TmaRing<kHistTmaStages> *tring = nullptr) {
     cg::cluster_group cluster = cg::this_cluster();
     const int C = MODE == kHistCluster ? int(cluster.num_blocks()) : 1;
     const int rank = MODE == kHistCluster ? int(cluster.block_rank()) : 0;
@@ -439,7 +459,6 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
 #pragma unroll
     for (int j = 0; j < D; ++j) stride[j] = g.d[j].stride;
     const bool tiled = (dl.s & 3) == 0;   // every row starts at the same alignment
-    constexpr int kSeg = 4 * 32 * kHistQmax - 4;
     // Visits every box: fn(box_lo, box_len, weight, r0, r1, kgfix).  With one
     // kernel in the group the last dimension is cut into its constant-
     // multiplicity pieces too, so every voxel of a box adds `weight` to
@@ -465,15 +484,15 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
             if (r1 <= r0) continue;
             if (single) {
                 for (int i = 0; i < pl.n; ++i)
-                    for (int x0 = pl.a[i]; x0 < pl.e[i]; x0 += kSeg) {
+                    for (int x0 = pl.a[i]; x0 < pl.e[i]; x0 += kHistSeg) {
                         box_lo[D - 1] = x0;
-                        len[D - 1] = min(kSeg, pl.e[i] - x0);
+                        len[D - 1] = min(kHistSeg, pl.e[i] - x0);
                         fn(box_lo, len, w * pl.m[i], r0, r1, 0);
                     }
             } else {
-                for (int x0 = xlo; x0 < xhi; x0 += kSeg) {   // segments along the last dim
+                for (int x0 = xlo; x0 < xhi; x0 += kHistSeg) {   // segments along the last dim
                     box_lo[D - 1] = x0;
-                    len[D - 1] = min(kSeg, xhi - x0);
+                    len[D - 1] = min(kHistSeg, xhi - x0);
                     fn(box_lo, len, w, r0, r1, -1);
                 }
             }
@@ -500,14 +519,25 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         }
     };
 
-    // rows [r0, r1) of a box in fixed quad slots (walk_tile), through the
-    // cp.async ring with RING
+    // rows [r0, r1) of a box in fixed quad slots: walk_tile, the cp.async
+    // ring, or TMA tiles (boxes that fit the tile's width)
     float4 *ring = reinterpret_cast<float4 *>(
         sh + hist_ring_offset_words(kKeysOnly ? 5 * size_t(G) : hist_smem_words(P, R, G)));
     auto walk = [&](auto sd_tag, const int *box_lo, const int *len, int r0, int r1,
                     const TileShape &ts, auto &&slot, auto &&quad) {
         using SD = typename decltype(sd_tag)::type;
-        if constexpr (RING) {
+        if constexpr (HW == kHistTma) {
+            if ((box_lo[D - 1] & 3) + len[D - 1] <= htma->bx) {
+                walk_tile_tma<D, kHistTmaStages, kHistTileFloats / 1024, kHistTmaStage, SD>(
+                    htma->map, box_lo, len, r0, r1, htma->bx, htma->by, *tring, slot,
+                    [&](const SD &sd, int i, const float4 &v) {
+                        NoRow nr;
+                        quad(nr, sd, i, v, v, int64_t(0));
+                    });
+                return;
+            }
+        }
+        if constexpr (HW == kHistRing) {
             walk_tile_async<D, kHistQmax, kHistStages, NoRow, SD>(in, stride, box_lo, len, r0, r1, ts,
                                                                   ring, slot, no_row, quad);
         } else {

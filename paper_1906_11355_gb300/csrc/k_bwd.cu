@@ -334,8 +334,7 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
     const float *sc = reinterpret_cast<const float *>(ws + p.ws.scale);
     cudaError_t e;
 #define MCLAHE_ADJ(A, R)                                                                       \
-    e = cudaFuncSetAttribute(k_adj<D, A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                             int(smem_adj));                                                   \
+    e = ensure_smem(reinterpret_cast<const void *>(k_adj<D, A, R>), size_t(smem_adj));          \
     if (e != cudaSuccess) return e;                                                            \
     k_adj<D, A, R><<<grid, 256, smem_adj, st>>>(g, in, gout, lo, sc, part, chunks);
     if (g.mode == MCLAHE_RANGE_ADAPTIVE) {
@@ -346,7 +345,7 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
 #undef MCLAHE_ADJ
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t smem_lb = size_t(g.P) * sizeof(float) + size_t(g.nb) * sizeof(uint32_t);
-    e = cudaFuncSetAttribute(k_lutbwd<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_lb));
+    e = ensure_smem(reinterpret_cast<const void *>(k_lutbwd<D>), size_t(smem_lb));
     if (e != cudaSuccess) return e;
     k_lutbwd<D><<<unsigned(g.K), 256, smem_lb, st>>>(
         g, reinterpret_cast<const uint32_t *>(ws + p.ws.hist), reinterpret_cast<const float *>(ws + p.ws.lut),

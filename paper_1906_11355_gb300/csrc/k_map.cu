@@ -66,56 +66,17 @@ static size_t map_tma_smem(const Geom &g) {
     return map_table_bytes(g.D, g.P) + 128 + size_t(kTmaStages) * kTmaTileFloats * sizeof(float);
 }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// The driver's tensor-map encoder, through the runtime (no link to libcuda).
-static EncodeTiledFn encode_tiled() {
-    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nullptr;
-        return reinterpret_cast<EncodeTiledFn>(f);
-    }();
-    return fn;
-}
-
-// Tensor map of a volume (float32, dims innermost first) with the tile box.
-static cudaError_t encode_volume(CUtensorMap *m, const float *ptr, const Geom &g, int bx, int by,
-                                 int bz) {
-    const EncodeTiledFn enc = encode_tiled();
-    if (!enc) return cudaErrorNotSupported;
-    const int D = g.D;
-    cuuint64_t dims[4], strides[3];
-    cuuint32_t box[4], es[4] = {1, 1, 1, 1};
-    for (int i = 0; i < D; ++i) dims[i] = cuuint64_t(g.d[D - 1 - i].s);
-    for (int i = 1; i < D; ++i) strides[i - 1] = cuuint64_t(g.d[D - 1 - i].stride) * sizeof(float);
-    box[0] = cuuint32_t(bx);
-    box[1] = cuuint32_t(by);
-    box[2] = D == 4 ? cuuint32_t(bz) : 1u;
-    box[3] = 1u;
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, cuuint32_t(D),
-                           const_cast<float *>(ptr), dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <int D, bool A>
 static cudaError_t launch_map_tma_t(const mclahe_plan_s &p, const float *in, float *out,
                                     const unsigned char *ws, cudaStream_t st, unsigned grid, int bx,
                                     int by, int bz) {
     const size_t smem = map_tma_smem(p.g);
     CUtensorMap m_in, m_out;
-    cudaError_t e = encode_volume(&m_in, in, p.g, bx, by, bz);
-    if (e == cudaSuccess) e = encode_volume(&m_out, out, p.g, bx, by, bz);
+    const int box[4] = {bx, by, p.g.D == 4 ? bz : 1, 1};
+    cudaError_t e = encode_tensor_map(&m_in, in, p.g, box);
+    if (e == cudaSuccess) e = encode_tensor_map(&m_out, out, p.g, box);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_map_tma<D, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        e = ensure_smem(reinterpret_cast<const void *>(k_map_tma<D, A>), smem);
     if (e != cudaSuccess) return e;
     k_map_tma<D, A><<<grid, 256, smem, st>>>(
         p.g, m_in, m_out, in, out, reinterpret_cast<const float *>(ws + p.ws.lut),
@@ -128,8 +89,7 @@ template <int D, bool A, bool REPL>
 static cudaError_t launch_map_t(const mclahe_plan_s &p, const float *in, float *out,
                                 const unsigned char *ws, cudaStream_t st, unsigned grid,
                                 size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_map<D, A, REPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
+    cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_map<D, A, REPL>), smem);
     if (e != cudaSuccess) return e;
     k_map<D, A, REPL><<<grid, p.t.map_threads, smem, st>>>(
         p.g, in, out, reinterpret_cast<const float *>(ws + p.ws.lut),

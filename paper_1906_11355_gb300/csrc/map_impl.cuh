@@ -266,16 +266,27 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     struct MRow {
         float2 w[ADAPTIVE ? NC / 2 : (NC >= 4 ? NQ : 2)];
     };
-    auto row_fn = [&](const int *coords, int64_t, MRow &st) {
+    // The outer weight of outer corner o is f0[o_0] * (product over dims
+    // 1..D-2, left to right), f0 = (w0, w1) of dim 0: row_weights takes f0
+    // as given, so the TMA walk can split off dim 0 (see below).
+    auto row_weights = [&](const int *coords, float f0a, float f0b, MRow &st) {
         float wo[NO];
+        if constexpr (D >= 2) {
+            constexpr int NI = NO / 2;   // corners over dims 1..D-2
+            float in_[NI];
 #pragma unroll
-        for (int i = 0; i < NO; ++i) wo[i] = 1.0f;
+            for (int i = 0; i < NI; ++i) in_[i] = 1.0f;
 #pragma unroll
-        for (int j = 0; j < D - 1; ++j) {
-            const float w1 = float(2 * coords[j] + mb[j]) * inv2b[j];
-            const float w0 = 1.0f - w1;
+            for (int j = 1; j < D - 1; ++j) {
+                const float w1 = float(2 * coords[j] + mb[j]) * inv2b[j];
+                const float w0 = 1.0f - w1;
 #pragma unroll
-            for (int i = 0; i < NO; ++i) wo[i] *= ((i >> (D - 2 - j)) & 1) ? w1 : w0;
+                for (int i = 0; i < NI; ++i) in_[i] *= ((i >> (D - 2 - j)) & 1) ? w1 : w0;
+            }
+#pragma unroll
+            for (int o = 0; o < NO; ++o) wo[o] = ((o >> (D - 2)) & 1 ? f0b : f0a) * in_[o & (NI - 1)];
+        } else {
+            wo[0] = 1.0f;
         }
         if (ADAPTIVE) {
             float a[NA];
@@ -295,6 +306,14 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         } else {
             st.w[0] = make_float2(1.0f, 1.0f);
             st.w[1] = st.w[0];
+        }
+    };
+    auto row_fn = [&](const int *coords, int64_t, MRow &st) {
+        if constexpr (D >= 2) {
+            const float w1 = float(2 * coords[0] + mb[0]) * inv2b[0];
+            row_weights(coords, 1.0f - w1, w1, st);
+        } else {
+            row_weights(coords, 1.0f, 0.0f, st);
         }
     };
 
@@ -427,6 +446,13 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             qz[i] = rest / By;
         }
         const int lx = len[D - 1];
+        // per slot, the row weights without dim 0 (inner) in this lane's order,
+        // and which entries take dim 0's w1 (sel): tiles of one block differ
+        // only in the slice along dim 0
+        constexpr int NW = sizeof(MRow) / sizeof(float2);
+        MRow inner[QT];
+        uint32_t sel[QT];
+        int cur_blk = -1;
         for (int k = 0; k < nt; ++k) {
             const int stg = k % NS;
             if (!mbar_wait_bounded(bar0 + 8u * uint32_t(stg), uint32_t(k / NS) & 1u, kTmaWaitLimit) &&
@@ -434,6 +460,33 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                 atomicCAS(tma->status, 0u, uint32_t(MCLAHE_ERR_TIMEOUT));
             const Tile t = tile(k);
             const uint32_t sbase = stage0 + uint32_t(stg) * kStageBytes;
+            const int blk = (kb + k) / n0;
+            if (blk != cur_blk) {   // uniform over the block
+                cur_blk = blk;
+#pragma unroll
+                for (int i = 0; i < QT; ++i) {
+                    int coords[kMaxDim];
+                    coords[0] = t.c[R - 1];
+                    if (D == 4) {
+                        coords[1] = t.c[2] + qz[i];
+                        coords[2] = t.c[1] + qy[i];
+                    } else {
+                        coords[1] = t.c[1] + qy[i];
+                    }
+                    MRow s0, s1;
+                    row_weights(coords, 1.0f, 0.0f, s0);
+                    row_weights(coords, 0.0f, 1.0f, s1);
+                    sel[i] = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        // exactly one of the two is the product over dims 1..D-2
+                        inner[i].w[w] = make_float2(s0.w[w].x + s1.w[w].x, s0.w[w].y + s1.w[w].y);
+                        sel[i] |= (s1.w[w].x != 0.0f ? 1u : 0u) << (2 * w);
+                        sel[i] |= (s1.w[w].y != 0.0f ? 1u : 0u) << (2 * w + 1);
+                    }
+                }
+            }
+            const float f1 = float(2 * t.c[R - 1] + mb[0]) * inv2b[0], f0 = 1.0f - f1;
 #pragma unroll
             for (int i = 0; i < QT; ++i) {
                 if (!qv[i]) continue;
@@ -454,7 +507,10 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                     coords[1] = y;
                 }
                 MRow st;
-                row_fn(coords, 0, st);
+#pragma unroll
+                for (int w = 0; w < NW; ++w)
+                    st.w[w] = make_float2(((sel[i] >> (2 * w)) & 1u ? f1 : f0) * inner[i].w[w].x,
+                                          ((sel[i] >> (2 * w + 1)) & 1u ? f1 : f0) * inner[i].w[w].y);
                 const float vals[4] = {v.x, v.y, v.z, v.w};
                 float res[4];
                 map4(st, vals, float(2 * x + mb_l) * inv2b_l, res);

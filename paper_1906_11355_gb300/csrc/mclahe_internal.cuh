@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "mclahe.h"
@@ -80,6 +81,7 @@ struct Tuning {
     int map_threads;    // threads per mapping CTA
     int map_chunks;     // CTAs per inter-kernel cell in the mapping pass
     int map_tma;        // 1: stream 3- and 4-D cells as TMA tiles (where map_tma_box allows)
+    int hist_tma;       // 1: stream histogram rows as TMA tiles (where hist_tma_box allows)
     int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)
 };
 
@@ -182,20 +184,23 @@ struct Foot {
     int32_t ml, mh;          // main image
     int32_t ll, lh;          // reflected at the start
     int32_t rl, rh;          // reflected at the end
-    __device__ __forceinline__ int mult(int x) const {
+    __host__ __device__ __forceinline__ int mult(int x) const {
         return int(x >= ml && x < mh) + int(x >= ll && x < lh) + int(x >= rl && x < rh);
     }
 };
 
-__device__ __forceinline__ Foot footprint(const Dim &d, int k) {
+__host__ __device__ __forceinline__ int imin_(int a, int b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int imax_(int a, int b) { return a > b ? a : b; }
+
+__host__ __device__ __forceinline__ Foot footprint(const Dim &d, int k) {
     Foot f;
     const int P0 = k * d.b, P1 = P0 + d.b;          // padded interval
-    f.ml = max(P0 - d.p0, 0);
-    f.mh = min(P1 - d.p0, d.s);
+    f.ml = imax_(P0 - d.p0, 0);
+    f.mh = imin_(P1 - d.p0, d.s);
     if (f.mh < f.ml) f.mh = f.ml;
     // padded P < p0 maps to x = p0 - 1 - P
     if (P0 < d.p0) {
-        f.ll = d.p0 - min(P1, d.p0);
+        f.ll = d.p0 - imin_(P1, d.p0);
         f.lh = d.p0 - P0;
     } else {
         f.ll = f.lh = 0;
@@ -203,19 +208,19 @@ __device__ __forceinline__ Foot footprint(const Dim &d, int k) {
     // padded P >= p0 + s maps to x = 2s - 1 - (P - p0)
     if (P1 > d.p0 + d.s) {
         f.rl = 2 * d.s - (P1 - d.p0);
-        f.rh = 2 * d.s - max(P0 - d.p0, d.s);
+        f.rh = 2 * d.s - imax_(P0 - d.p0, d.s);
     } else {
         f.rl = f.rh = 0;
     }
     f.lo = f.ml;
     f.hi = f.mh;
     if (f.lh > f.ll) {
-        f.lo = min(f.lo, f.ll);
-        f.hi = max(f.hi, f.lh);
+        f.lo = imin_(f.lo, f.ll);
+        f.hi = imax_(f.hi, f.lh);
     }
     if (f.rh > f.rl) {
-        f.lo = min(f.lo, f.rl);
-        f.hi = max(f.hi, f.rh);
+        f.lo = imin_(f.lo, f.rl);
+        f.hi = imax_(f.hi, f.rh);
     }
     return f;
 }
@@ -226,7 +231,7 @@ struct Pieces {
     int a[kMaxPieces], e[kMaxPieces], m[kMaxPieces];   // [a, e) with multiplicity m
 };
 
-__device__ __forceinline__ Pieces footprint_pieces(const Dim &d, int k) {
+__host__ __device__ __forceinline__ Pieces footprint_pieces(const Dim &d, int k) {
     Pieces p;
     {   // interior kernel: one piece, the main image, multiplicity 1
         const int a = k * d.b - d.p0;
@@ -742,15 +747,26 @@ cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float
                             unsigned char *ws, const float *d_clip, float *d_grad_lut,
                             float *d_grad_clip, cudaStream_t st);
 size_t bwd_partial_floats(const Geom &g, int chunks);
-// Dynamic shared memory of a histogram CTA (with the row ring of the
-// per-volume launches, without it in the batched launch).
-size_t hist_smem_bytes(const Geom &g, int copies, int group, bool ring = true);
+// Dynamic shared memory of a histogram CTA for a row walk (0: per-thread
+// loads, the batched launch; 1: the cp.async row ring; 2: TMA tiles), and of
+// the flat form's range pass.
+size_t hist_smem_bytes(const Geom &g, int copies, int group, int walk = 1);
+size_t hist_range_smem_bytes(int group, int walk);
+bool hist_tma_box(const Geom &g, int group, int &bx, int &by);
+// Tensor map of a float32 volume (dims innermost first) with box[0..D-1]
+// elements per tile (tma_host.cu).
+cudaError_t encode_tensor_map(CUtensorMap *m, const float *ptr, const Geom &g, const int *box);
 cudaError_t launch_hist_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                               cudaStream_t st);
 int64_t hist_items(const Geom &g, int group);
 size_t map_smem_bytes(const Geom &g);
 bool map_tma_box(const Geom &g, int &bx, int &by, int &bz);
 bool map_replicated(const Geom &g);
+
+// launch_cache.cu: raise a kernel's dynamic shared-memory limit (once per
+// device, kernel and size) and cached occupancy (CTAs per SM)
+cudaError_t ensure_smem(const void *func, size_t bytes);
+cudaError_t cached_occupancy(const void *func, int threads, size_t smem, int *per_sm);
 
 // batch.cu
 void batch_forget_plan(const mclahe_plan_s *p);

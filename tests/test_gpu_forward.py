@@ -151,6 +151,36 @@ def test_tma_mapping_matches_oracle(torch_cuda, orc, case, chunks):
     assert nat.mclahe_sync_status(op.ws) == 0
 
 
+# the histogram pass on TMA box tiles: 2- to 4-D, both range modes, cluster and
+# flat forms, mirror pieces that start off a 16-byte boundary
+TMA_HIST_CASES = [
+    ((64, 64), (16, 16), 256, 0.02, False),
+    ((40, 56), (5, 7), 64, 0.03, True),
+    ((16, 64, 64), (4, 16, 16), 256, 0.02, True),
+    ((13, 37, 36), (4, 6, 12), 256, 0.02, False),
+    ((6, 10, 12, 16), (3, 5, 4, 8), 512, 0.01, False),
+    ((9, 11, 14, 20), (3, 4, 5, 4), 50, 0.05, True),
+]
+TMA_HIST_FORMS = [dict(hist_group=1, hist_cluster=2, hist_copies=4, hist_shares=0),
+                  dict(hist_group=2, hist_cluster=1, hist_copies=8, hist_shares=7),
+                  dict(hist_group=1, hist_cluster=1, hist_copies=16, hist_shares=300)]
+
+
+@pytest.mark.parametrize("form", range(len(TMA_HIST_FORMS)))
+@pytest.mark.parametrize("case", TMA_HIST_CASES,
+                         ids=[str(c[0]) + ("A" if c[4] else "G") for c in TMA_HIST_CASES])
+def test_tma_histogram_matches_oracle(torch_cuda, orc, case, form):
+    from paper_1906_11355_gb300 import _native as nat
+
+    shape, ks, nb, clip, adaptive = case
+    rng = np.random.default_rng(hash((shape, ks, nb, form, 7)) % 2**32)
+    x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
+    shapes = dict(TMA_HIST_FORMS[form], map_chunks=1, hist_tma=1)
+    op, _, _ = run_case(torch_cuda, orc, x, ks, nb, clip, adaptive, shapes=shapes)
+    assert op.shapes()["hist_tma"] == 1
+    assert nat.mclahe_sync_status(op.ws) == 0
+
+
 def test_tma_mapping_rejected_where_rows_are_unaligned(torch_cuda):
     from paper_1906_11355_gb300.api import MCLAHE
     from paper_1906_11355_gb300 import _native as nat

@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default launch shapes (mclahe_autotune is skipped)")
+    ap.add_argument("--shapes", default=None,
+                    help="launch shapes as JSON (the keys of MCLAHE.set_shapes) instead of autotuning")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and forward+backward forms")
@@ -427,7 +429,9 @@ def run_native(args):
                 adaptive=w["adaptive"], device=dev)
     x = torch.from_numpy(x_host).to(dev)
     out = torch.empty_like(x)
-    if not args.no_autotune:
+    if args.shapes:
+        op.set_shapes(**json.loads(args.shapes))
+    elif not args.no_autotune:
         op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
     shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
               if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_tma",

@@ -482,19 +482,26 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
             const int r0 = int((int64_t(rows) * sh0) / nsh);
             const int r1 = int((int64_t(rows) * sh1) / nsh);
             if (r1 <= r0) continue;
-            if (single) {
-                for (int i = 0; i < pl.n; ++i)
-                    for (int x0 = pl.a[i]; x0 < pl.e[i]; x0 += kHistSeg) {
+            // [a, e) along the last dim in ceil((e - a) / kHistSeg) segments of
+            // about equal length, inner boundaries on 16-byte boundaries
+            // (every segment fits a walk's 512-element row: head + length)
+            auto segments = [&](int a, int e, int wt, int kgfix) {
+                const int n = (e - a + kHistSeg - 1) / kHistSeg;
+                int x0 = a;
+                for (int i = 1; i <= n; ++i) {
+                    const int x1 = i == n ? e : ((a + int((int64_t(e - a) * i) / n)) & ~3);
+                    if (x1 > x0) {
                         box_lo[D - 1] = x0;
-                        len[D - 1] = min(kHistSeg, pl.e[i] - x0);
-                        fn(box_lo, len, w * pl.m[i], r0, r1, 0);
+                        len[D - 1] = x1 - x0;
+                        fn(box_lo, len, wt, r0, r1, kgfix);
                     }
-            } else {
-                for (int x0 = xlo; x0 < xhi; x0 += kHistSeg) {   // segments along the last dim
-                    box_lo[D - 1] = x0;
-                    len[D - 1] = min(kHistSeg, xhi - x0);
-                    fn(box_lo, len, w, r0, r1, -1);
+                    x0 = x1;
                 }
+            };
+            if (single) {
+                for (int i = 0; i < pl.n; ++i) segments(pl.a[i], pl.e[i], w * pl.m[i], 0);
+            } else {
+                segments(xlo, xhi, w, -1);
             }
         }
     };
@@ -523,6 +530,18 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     // ring, or TMA tiles (boxes that fit the tile's width)
     float4 *ring = reinterpret_cast<float4 *>(
         sh + hist_ring_offset_words(kKeysOnly ? 5 * size_t(G) : hist_smem_words(P, R, G)));
+    // whole-quad boxes: every slot of every row is a full quad (head 0 and
+    // L = 4 * LPR * QL with QL = kHistQmax), walked without per-slot tests
+    // and counted by quad_full
+    auto whole_quads = [&](const int *len, const TileShape &ts) {
+        return ts.head == 0 && ts.QL == kHistQmax && len[D - 1] == 4 * ts.LPR * kHistQmax;
+    };
+    auto walk_full = [&](auto sd_tag, const int *box_lo, const int *len, int r0, int r1,
+                         const TileShape &ts, auto &&slot, auto &&quad_full) {
+        using SD = typename decltype(sd_tag)::type;
+        walk_tile_async<D, kHistQmax, kHistStages, NoRow, SD, true>(in, stride, box_lo, len, r0, r1, ts,
+                                                                    ring, slot, no_row, quad_full);
+    };
     auto walk = [&](auto sd_tag, const int *box_lo, const int *len, int r0, int r1,
                     const TileShape &ts, auto &&slot, auto &&quad) {
         using SD = typename decltype(sd_tag)::type;
@@ -610,7 +629,18 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                         }
                     }
                 };
-                walk(Tag<MSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
+                if (HW == kHistRing && kgfix >= 0 && whole_quads(len, ts)) {
+                    auto quad_full = [&](NoRow &, const MSlot &, int i, const float4 &v, const float4 &,
+                                         int64_t) {
+                        mn[i] = min3f(mn[i], v.x, v.y);
+                        mn[i] = min3f(mn[i], v.z, v.w);
+                        mx[i] = max3f(mx[i], v.x, v.y);
+                        mx[i] = max3f(mx[i], v.z, v.w);
+                    };
+                    walk_full(Tag<MSlot>{}, box_lo, len, r0, r1, ts, slot, quad_full);
+                } else {
+                    walk(Tag<MSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
+                }
                 // warp-aggregated: one pair of shared atomics per warp and
                 // target kernel (256 threads' atomics on one key serialise)
 #pragma unroll
@@ -737,7 +767,20 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                             if (sd.q0 + e >= 0 && sd.q0 + e < L) red_shared_add(bits[e] * r4 + base, wu);
                     }
                 };
-                walk(Tag<FSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
+                if (HW == kHistRing && whole_quads(len, ts)) {
+                    auto quad_full = [&](NoRow &, const FSlot &, int, const float4 &v, const float4 &,
+                                         int64_t) {
+                        const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
+                        const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
+                        red_shared_add(b01.x * r4 + base, wu);
+                        red_shared_add(b01.y * r4 + base, wu);
+                        red_shared_add(b23.x * r4 + base, wu);
+                        red_shared_add(b23.y * r4 + base, wu);
+                    };
+                    walk_full(Tag<FSlot>{}, box_lo, len, r0, r1, ts, slot, quad_full);
+                } else {
+                    walk(Tag<FSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
+                }
             } else if (tiled) {
                 // groups of kernels: a slot's quad goes to one kernel (with
                 // one multiplicity) when its first and last voxel do -- the

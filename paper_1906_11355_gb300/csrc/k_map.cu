@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256, D >= 4 ? (ADAPTIVE ? 1 : 2) : (ADAPTIVE &
 // along dims D-2 and (4-D) 1 as fit in kTmaTileFloats, dividing the kernel
 // size so interior cells split into whole tiles.
 template <int D, bool ADAPTIVE>
-__global__ void __launch_bounds__(256, D >= 4 ? (ADAPTIVE ? 1 : 2) : 2)
+__global__ void __launch_bounds__(kTmaConsumers + 32, D >= 4 ? (ADAPTIVE ? 1 : 2) : 2)
     k_map_tma(Geom g, const __grid_constant__ CUtensorMap tm_in,
               const __grid_constant__ CUtensorMap tm_out, const float *__restrict__ in,
               float *__restrict__ out, const float *__restrict__ lut,
@@ -78,7 +78,7 @@ static cudaError_t launch_map_tma_t(const mclahe_plan_s &p, const float *in, flo
     if (e == cudaSuccess)
         e = ensure_smem(reinterpret_cast<const void *>(k_map_tma<D, A>), smem);
     if (e != cudaSuccess) return e;
-    k_map_tma<D, A><<<grid, 256, smem, st>>>(
+    k_map_tma<D, A><<<grid, kTmaConsumers + 32, smem, st>>>(
         p.g, m_in, m_out, in, out, reinterpret_cast<const float *>(ws + p.ws.lut),
         reinterpret_cast<const float *>(ws + p.ws.lo), reinterpret_cast<const float *>(ws + p.ws.scale),
         p.t.map_chunks, bx, by, bz, reinterpret_cast<uint32_t *>(const_cast<unsigned char *>(ws) + p.ws.status));

@@ -54,7 +54,8 @@ namespace mclahe {
 //              in the other walks; TMA moves whole boxes instead.
 constexpr int kWalkLsu = 0, kWalkRing = 1, kWalkTma = 2;
 constexpr int kTmaStages = 4;
-constexpr int kTmaTileFloats = 2048;   // at most; 2 quads per thread of 256
+constexpr int kTmaTileFloats = 2048;   // at most; 2 quads per consumer thread
+constexpr int kTmaConsumers = 256;     // mapping threads; one more warp moves the tiles
 constexpr uint32_t kTmaWaitLimit = 1u << 22;
 
 // The tile box and tensor maps of a TMA mapping launch.  The box spans the
@@ -382,16 +383,24 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     };
 
     if constexpr (WALK == kWalkTma) {
+        // Warp-specialised tile pipeline: warps 0..7 map (kTmaConsumers
+        // threads), warp 8 moves tiles.  Stage s has a "full" barrier (the
+        // producer's expect_tx; the TMA load completes it) and an "empty"
+        // barrier (one arrival per consumer warp once its results are in the
+        // stage).  The producer stores a finished full tile back with TMA, waits
+        // for the store to have read the stage, then loads the next tile into it.
         static_assert(D >= 3 && REPL, "TMA tiles: 3- and 4-D cells, replicated tables");
         constexpr int NS = kTmaStages;
-        constexpr int QT = kTmaTileFloats / 4 / 256;   // quad slots per thread
-        constexpr int R = D;                           // box rank
+        constexpr int NCW = kTmaConsumers / 32;                 // consumer warps
+        constexpr int QT = kTmaTileFloats / 4 / kTmaConsumers;  // quad slots per consumer thread
+        constexpr int R = D;                                    // box rank
         const int Bx = tma->bx, By = tma->by, Bz = D == 4 ? tma->bz : 1;
         const int tile_q = (Bx * By * Bz) >> 2;
         const uint32_t tile_bytes = uint32_t(Bx * By * Bz) * 4u;
         constexpr uint32_t kStageBytes = kTmaTileFloats * 4;
-        __shared__ __align__(8) uint64_t s_bar[NS];
-        const uint32_t bar0 = uint32_t(__cvta_generic_to_shared(s_bar));
+        __shared__ __align__(8) uint64_t s_full[NS], s_empty[NS];
+        const uint32_t full0 = uint32_t(__cvta_generic_to_shared(s_full));
+        const uint32_t empty0 = uint32_t(__cvta_generic_to_shared(s_empty));
         const uint32_t stage0 = (tab_s + uint32_t(map_table_bytes(D, P)) + 127u) & ~127u;
         // tiles of this cell: slices along dim 0 innermost, then blocks along
         // dim D-2, then (4-D) along dim 1; this CTA takes a contiguous range
@@ -418,26 +427,58 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                      (D < 4 || (zb + 1) * Bz <= len[1]);
             return t;
         };
-        auto issue = [&](int k) {
-            const Tile t = tile(k);
-            const uint32_t bar = bar0 + 8u * uint32_t(k % NS);
-            mbar_expect_tx(bar, tile_bytes);
-            tma_load<R>(stage0 + uint32_t(k % NS) * kStageBytes, tma->in, t.c, bar);
+        auto gave_up = [&]() {
+            if (tma->status) atomicCAS(tma->status, 0u, uint32_t(MCLAHE_ERR_TIMEOUT));
         };
         if (threadIdx.x == 0) {
 #pragma unroll
-            for (int i = 0; i < NS; ++i) mbar_init(bar0 + 8u * i, 1);
+            for (int i = 0; i < NS; ++i) {
+                mbar_init(full0 + 8u * i, 1);
+                mbar_init(empty0 + 8u * i, NCW);
+            }
             mbar_init_fence();
         }
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int k = 0; k < NS - 1 && k < nt; ++k) issue(k);
-        // this thread's quads of a tile: in-tile coordinates (fixed)
+        const int warp = int(threadIdx.x) >> 5;
+        if (warp == NCW) {
+            // ---- producer (one lane)
+            if (lane == 0) {
+                auto load = [&](int k) {
+                    const Tile t = tile(k);
+                    const uint32_t st = uint32_t(k % NS);
+                    mbar_expect_tx(full0 + 8u * st, tile_bytes);
+                    tma_load<R>(stage0 + st * kStageBytes, tma->in, t.c, full0 + 8u * st);
+                };
+                // tile k - NS is finished when its stage's empty barrier
+                // completes its ((k / NS) - 1)-th phase; store it if full
+                auto retire = [&](int k) {
+                    const uint32_t st = uint32_t(k % NS);
+                    if (!mbar_wait_bounded(empty0 + 8u * st, uint32_t(k / NS) & 1u, kTmaWaitLimit))
+                        gave_up();
+                    const Tile t = tile(k);
+                    if (t.full) {
+                        tma_store<R>(tma->out, t.c, stage0 + st * kStageBytes);
+                        bulk_commit();
+                    }
+                };
+                for (int k = 0; k < nt; ++k) {
+                    if (k >= NS) {
+                        retire(k - NS);
+                        bulk_wait_read<0>();   // the store has read the stage
+                    }
+                    load(k);
+                }
+                for (int k = nt > NS ? nt - NS : 0; k < nt; ++k) retire(k);
+                bulk_wait_all();
+            }
+            return;
+        }
+        // ---- consumers: this thread's quads of a tile, in-tile coordinates
         int qx[QT], qy[QT], qz[QT];
         bool qv[QT];
 #pragma unroll
         for (int i = 0; i < QT; ++i) {
-            const int qi = int(threadIdx.x) + i * int(blockDim.x);
+            const int qi = int(threadIdx.x) + i * kTmaConsumers;
             qv[i] = qi < tile_q;
             const int e = 4 * qi;
             qx[i] = e % Bx;
@@ -455,13 +496,12 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         int cur_blk = -1;
         for (int k = 0; k < nt; ++k) {
             const int stg = k % NS;
-            if (!mbar_wait_bounded(bar0 + 8u * uint32_t(stg), uint32_t(k / NS) & 1u, kTmaWaitLimit) &&
-                tma->status)
-                atomicCAS(tma->status, 0u, uint32_t(MCLAHE_ERR_TIMEOUT));
+            if (!mbar_wait_bounded(full0 + 8u * uint32_t(stg), uint32_t(k / NS) & 1u, kTmaWaitLimit))
+                gave_up();
             const Tile t = tile(k);
             const uint32_t sbase = stage0 + uint32_t(stg) * kStageBytes;
             const int blk = (kb + k) / n0;
-            if (blk != cur_blk) {   // uniform over the block
+            if (blk != cur_blk) {
                 cur_blk = blk;
 #pragma unroll
                 for (int i = 0; i < QT; ++i) {
@@ -496,16 +536,8 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                 const bool in_cell = qx[i] < lx && y < box_lo[D - 2] + len[D - 2] &&
                                      (D < 4 || z < box_lo[1] + len[1]);
                 if (!in_cell) continue;
-                const uint32_t qa = sbase + 16u * uint32_t(int(threadIdx.x) + i * int(blockDim.x));
+                const uint32_t qa = sbase + 16u * uint32_t(int(threadIdx.x) + i * kTmaConsumers);
                 const float4 v = lds128(qa);
-                int coords[kMaxDim];
-                coords[0] = t.c[R - 1];
-                if (D == 4) {
-                    coords[1] = z;
-                    coords[2] = y;
-                } else {
-                    coords[1] = y;
-                }
                 MRow st;
 #pragma unroll
                 for (int w = 0; w < NW; ++w)
@@ -515,32 +547,28 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                 float res[4];
                 map4(st, vals, float(2 * x + mb_l) * inv2b_l, res);
                 if (t.full) {
-                    // in place: the tile goes back with one TMA store
+                    // in place: the producer stores the tile with one TMA store
                     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(qa), "f"(res[0]),
                                  "f"(res[1]), "f"(res[2]), "f"(res[3])
                                  : "memory");
                 } else {
                     int64_t a = x;
-#pragma unroll
-                    for (int j = 0; j < D - 1; ++j) a += int64_t(coords[j]) * stride[j];
+                    a += int64_t(t.c[R - 1]) * stride[0];
+                    if (D == 4) {
+                        a += int64_t(z) * stride[1];
+                        a += int64_t(y) * stride[2];
+                    } else {
+                        a += int64_t(y) * stride[1];
+                    }
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
                         if (qx[i] + e < lx) out[a + e] = res[e];
                 }
             }
             if (t.full) fence_proxy_async_smem();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (t.full) tma_store<R>(tma->out, t.c, sbase);
-                bulk_commit();
-                const int kn = k + NS - 1;
-                if (kn < nt) {
-                    bulk_wait_read<1>();   // the store of tile k - 1 has read its stage
-                    issue(kn);
-                }
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8u * uint32_t(stg));
         }
-        if (threadIdx.x == 0) bulk_wait_all();
         return;
     }
 

@@ -642,8 +642,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int D, int QMAX, int ST, typename S, typename SD, typename SlotFn, typename RowFn,
-          typename QuadFn>
+// FULL: the caller has checked that every slot of every row is a whole quad
+// inside the box (head 0, L = 4 * LPR * QMAX): no per-slot tests.
+template <int D, int QMAX, int ST, typename S, typename SD, bool FULL = false, typename SlotFn,
+          typename RowFn, typename QuadFn>
 __device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, const int64_t *stride,
                                                 const int *box_lo, const int *box_len, int r0,
                                                 int r1, const TileShape &t, float4 *ring,
@@ -684,7 +686,7 @@ __device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, co
         const int64_t a0 = row_addr(iss, coords);
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
-            if (ok[i]) cp_async16(slot_addr(stage, i), in + a0 + i * step);
+            if (FULL || ok[i]) cp_async16(slot_addr(stage, i), in + a0 + i * step);
     };
 #pragma unroll
     for (int k = 0; k < ST - 1; ++k) {
@@ -702,7 +704,7 @@ __device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, co
         row_fn(coords, st);
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
-            if (ok[i]) {
+            if (FULL || ok[i]) {
                 const float4 v = lds128(slot_addr(stage_c, i));
                 quad_fn(st, sd[i], i, v, v, a0 + i * step);
             }

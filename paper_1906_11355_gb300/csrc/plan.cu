@@ -68,11 +68,9 @@ Tuning default_tuning(const Geom &g) {
                      (items * C < sms && vitem / (2 * C) >= 16 * 1024)))
         C <<= 1;
     t.hist_chunks = C;
-    // flat form: about 16 shares per CTA of one wave (the launch bounds' CTAs
-    // per SM), so the CTAs' work differs by at most about 1/16
-    const int64_t wave = int64_t(sms) * (g.D >= 4 ? 2 : 3);
-    const int64_t item_rows = std::max<int64_t>(g.V / dl.b, 1);
-    t.hist_shares = int(std::min<int64_t>(std::min<int64_t>((16 * wave + items - 1) / items, 256), item_rows));
+    // the cluster form (the flat form and TMA rows are autotuner candidates;
+    // neither won on the benchmark volumes)
+    t.hist_shares = 0;
     int64_t rows = 1, cell_vox = dl.b;   // rows and voxels of an interior cell
     for (int j = 0; j + 1 < g.D; ++j) {
         rows *= g.d[j].b;
@@ -86,7 +84,7 @@ Tuning default_tuning(const Geom &g) {
     // requests would touch a line per 32 bytes
     int bx, by, bz;
     t.map_tma = (map_tma_box(g, bx, by, bz) && dl.b < 32) ? 1 : 0;
-    t.hist_tma = hist_tma_box(g, t.hist_group, bx, by) ? 1 : 0;
+    t.hist_tma = 0;
     int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
     t.bwd_chunks = int(std::min<int64_t>(bc, 32));

@@ -180,7 +180,7 @@ def algorithmic_bytes(info, adaptive, has_range):
 def kernel_source_hash(pass_name):
     """Hash of the sources a pass's kernel is compiled from (the recorded ncu
     traffic is only reported while this matches)."""
-    hist = ("k_hist.cu", "k_hist_tma.cu", "k_hist_impl.cuh", "hist_impl.cuh", "tma.cuh")
+    hist = ("k_hist.cu", "k_hist_tma.cu", "k_hist_lsu.cu", "k_hist_impl.cuh", "hist_impl.cuh", "tma.cuh")
     files = {"range": ("k_range.cu",) + hist, "hist": hist,
              "map": ("k_map.cu", "map_impl.cuh", "tma.cuh")}[pass_name]
     h = hashlib.sha256()
@@ -434,7 +434,7 @@ def run_native(args):
     elif not args.no_autotune:
         op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
     shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
-              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_tma",
+              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk",
                        "map_chunks", "map_tma", "tuned")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -124,7 +124,8 @@ typedef struct {
     int32_t hist_ctas;            /* CTAs of the flat histogram pass at its last launch (0 if
                                      not flat or not launched yet) */
     int32_t map_tma;              /* 1: the mapping pass streams its cells as TMA box tiles */
-    int32_t hist_tma;             /* 1: the histogram pass streams its rows as TMA box tiles */
+    int32_t hist_walk;            /* rows of the histogram pass: 0 cp.async ring, 1 TMA box
+                                     tiles, 2 per-thread loads (least shared memory) */
 } mclahe_plan_info;
 
 /*
@@ -267,19 +268,20 @@ MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, 
  *   hist_cluster  CTAs per work item (a cluster): 1, 2, 4 or 8; 1 if hist_shares > 0.
  *   hist_copies   lane copies of the shared-memory histograms: 1, 2, 4, ..., 32.
  *   hist_shares   0: cluster form; 1..4096: flat form with that many shares per item.
- *   hist_tma      0: per-thread cp.async row ring; 1: TMA box tiles (2- to 4-D volumes
+ *   hist_walk     0: per-thread cp.async row ring; 1: TMA box tiles (2- to 4-D volumes
  *                 whose last extent is a multiple of 4, footprint rows of at most 256
- *                 elements per tile).
+ *                 elements per tile); 2: per-thread loads into registers (no row buffer
+ *                 in shared memory).
  *   map_chunks    CTAs per inter-kernel cell in the mapping pass, 1..64.
  *   map_tma       0: per-thread loads and stores; 1: TMA box tiles (3- and 4-D volumes
  *                 whose last dim and cell rows start on 16-byte boundaries only).
  * Returns MCLAHE_ERR_INVALID_ARG (plan unchanged) for values outside these
- * ranges, a histogram CTA above 220 KiB of shared memory, or hist_tma = 1 or
+ * ranges, a histogram CTA above 220 KiB of shared memory, or hist_walk = 1 or
  * map_tma = 1 on a geometry that does not allow it.  Sets tuned = 2.
  */
 MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist_group,
                                                 int32_t hist_cluster, int32_t hist_copies,
-                                                int32_t hist_shares, int32_t hist_tma,
+                                                int32_t hist_shares, int32_t hist_walk,
                                                 int32_t map_chunks, int32_t map_tma);
 
 /* Size of the library's built-in scratch array used by mclahe_forward_noalloc. */

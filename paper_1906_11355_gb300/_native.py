@@ -59,7 +59,7 @@ class PlanInfo(ctypes.Structure):
         ("hist_copies", ctypes.c_int32), ("map_chunks", ctypes.c_int32),
         ("bwd_chunks", ctypes.c_int32), ("tuned", ctypes.c_int32),
         ("hist_shares", ctypes.c_int32), ("hist_ctas", ctypes.c_int32),
-        ("map_tma", ctypes.c_int32), ("hist_tma", ctypes.c_int32),
+        ("map_tma", ctypes.c_int32), ("hist_walk", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -208,9 +208,9 @@ def mclahe_plan_query(plan) -> dict:
 
 
 def mclahe_plan_set_shapes(plan, hist_group, hist_cluster, hist_copies, hist_shares, map_chunks,
-                           map_tma=0, hist_tma=0):
+                           map_tma=0, hist_walk=0):
     _check(load().mclahe_plan_set_shapes(plan.handle, int(hist_group), int(hist_cluster),
-                                         int(hist_copies), int(hist_shares), int(hist_tma),
+                                         int(hist_copies), int(hist_shares), int(hist_walk),
                                          int(map_chunks), int(map_tma)),
            "mclahe_plan_set_shapes")
 

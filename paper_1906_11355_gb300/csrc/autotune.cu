@@ -106,16 +106,18 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
     for (int j = 0; j + 1 < p->g.D; ++j) item_rows *= p->g.d[j].b;
     for (int G : groups) {
         for (int R = 2; R <= 32 && s == MCLAHE_OK; R <<= 1) {
-            if (hist_smem_bytes(p->g, R, G) > 200 * 1024) continue;
+            if (hist_smem_bytes(p->g, R, G, 0) > 200 * 1024) continue;
             p->t.hist_group = G;
             p->t.hist_copies = R;
             // cluster form: C CTAs per item; flat form: S shares per item
             int bx, by;
-            const int n_walks = hist_tma_box(p->g, G, bx, by) ? 2 : 1;
-            for (int v = 0; v < (4 + 9) * n_walks; ++v) {
+            const bool tma_ok = hist_tma_box(p->g, G, bx, by);
+            for (int v = 0; v < (4 + 9) * 3; ++v) {
                 const int f = v % 13;
-                p->t.hist_tma = v / 13;
-                if (p->t.hist_tma && hist_smem_bytes(p->g, R, G, 2) > 200 * 1024) continue;
+                p->t.hist_walk = v / 13;   // ring, TMA tiles, per-thread loads
+                if (p->t.hist_walk == 1 && !tma_ok) continue;
+                const int code = p->t.hist_walk == 0 ? 1 : p->t.hist_walk == 1 ? 2 : 0;
+                if (hist_smem_bytes(p->g, R, G, code) > 200 * 1024) continue;
                 if (f < 4) {
                     p->t.hist_chunks = 1 << f;
                     p->t.hist_shares = 0;
@@ -133,7 +135,7 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
                     best.hist_chunks = p->t.hist_chunks;
                     best.hist_shares = p->t.hist_shares;
                     best.hist_copies = R;
-                    best.hist_tma = p->t.hist_tma;
+                    best.hist_walk = p->t.hist_walk;
                 }
             }
         }

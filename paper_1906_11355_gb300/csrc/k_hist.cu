@@ -1,6 +1,7 @@
 // k_hist.cu -- the histogram pass of one volume: shapes, shared-memory sizes,
-// the TMA box, and the launches with the cp.async row ring (the TMA-tile
-// launches are in k_hist_tma.cu; kernels in k_hist_impl.cuh).
+// the TMA box, and the launches with the cp.async row ring (the TMA-tile and
+// per-thread-load launches are in k_hist_tma.cu and k_hist_lsu.cu; kernels in
+// k_hist_impl.cuh).
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
@@ -20,7 +21,8 @@ size_t hist_smem_bytes(const Geom &g, int copies, int group, int walk) {
 size_t hist_range_smem_bytes(int group, int walk) {
     const size_t words = 5 * size_t(group);
     if (walk == kHistTma) return words * sizeof(uint32_t) + 128 + size_t(kHistTmaStages) * kHistTmaStage;
-    return hist_ring_offset_words(words) * sizeof(uint32_t) + hist_ring_bytes(256);
+    if (walk == kHistRing) return hist_ring_offset_words(words) * sizeof(uint32_t) + hist_ring_bytes(256);
+    return words * sizeof(uint32_t);
 }
 
 int64_t hist_items(const Geom &g, int group) {
@@ -61,12 +63,15 @@ bool hist_tma_box(const Geom &g, int G, int &bx, int &by) {
 
 cudaError_t launch_hist_tma(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                             const float *d_clip, cudaStream_t st, bool range, int bx, int by);
+cudaError_t launch_hist_lsu(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+                            const float *d_clip, cudaStream_t st, bool range);
 
 static cudaError_t launch_any(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                               const float *d_clip, cudaStream_t st, bool range) {
     int bx, by;
-    if (p.t.hist_tma && hist_tma_box(p.g, p.t.hist_group, bx, by))
+    if (p.t.hist_walk == 1 && hist_tma_box(p.g, p.t.hist_group, bx, by))
         return launch_hist_tma(p, in, ws, d_clip, st, range, bx, by);
+    if (p.t.hist_walk == 2) return launch_hist_lsu(p, in, ws, d_clip, st, range);
     HistTmaArgs none;
     std::memset(&none.map, 0, sizeof(none.map));
     return launch_hist_walk<kHistRing>(p, in, ws, d_clip, st, none, range);

@@ -1,7 +1,8 @@
 // k_hist_impl.cuh -- kernels and launcher templates of the histogram pass of
 // one volume (Algorithm 1; the work on one group of kernels along the last
 // dimension is in hist_impl.cuh), instantiated per row walk (HW) in k_hist.cu
-// (cp.async ring) and k_hist_tma.cu (TMA tiles).  Two forms:
+// (cp.async ring), k_hist_tma.cu (TMA tiles) and k_hist_lsu.cu (per-thread
+// loads).  Two forms:
 //   cluster: one thread-block cluster per group builds its histograms and
 //            mapping tables;
 //   flat:    every group is cut into equal shares of its rows, and the shares

@@ -84,7 +84,7 @@ Tuning default_tuning(const Geom &g) {
     // requests would touch a line per 32 bytes
     int bx, by, bz;
     t.map_tma = (map_tma_box(g, bx, by, bz) && dl.b < 32) ? 1 : 0;
-    t.hist_tma = 0;
+    t.hist_walk = 0;
     int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
     t.bwd_chunks = int(std::min<int64_t>(bc, 32));
@@ -289,7 +289,7 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->hist_shares = p->t.hist_shares;
     info->hist_ctas = p->t.hist_shares > 0 ? p->flat_ctas : 0;
     info->map_tma = p->t.map_tma;
-    info->hist_tma = p->t.hist_tma;
+    info->hist_walk = p->t.hist_walk;
     info->hist_copies = p->t.hist_copies;
     info->map_chunks = p->t.map_chunks;
     info->bwd_chunks = p->t.bwd_chunks;
@@ -298,7 +298,7 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
 }
 
 mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_t hist_cluster,
-                                     int32_t hist_copies, int32_t hist_shares, int32_t hist_tma,
+                                     int32_t hist_copies, int32_t hist_shares, int32_t hist_walk,
                                      int32_t map_chunks, int32_t map_tma) {
     if (!p) return MCLAHE_ERR_INVALID_ARG;
     auto pow2 = [](int32_t v, int32_t hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
@@ -310,9 +310,11 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     if (map_chunks < 1 || map_chunks > 64) return MCLAHE_ERR_INVALID_ARG;
     int bx, by, bz;
     if (map_tma != 0 && (map_tma != 1 || !map_tma_box(g, bx, by, bz))) return MCLAHE_ERR_INVALID_ARG;
-    if (hist_tma != 0 && (hist_tma != 1 || !hist_tma_box(g, hist_group, bx, by)))
+    if (hist_walk < 0 || hist_walk > 2 || (hist_walk == 1 && !hist_tma_box(g, hist_group, bx, by)))
         return MCLAHE_ERR_INVALID_ARG;
-    if (hist_smem_bytes(g, hist_copies, hist_group, hist_tma ? 2 : 1) > 220 * 1024)
+    // walk codes of hist_smem_bytes: 1 ring, 2 TMA, 0 per-thread loads
+    const int walk_code = hist_walk == 0 ? 1 : hist_walk == 1 ? 2 : 0;
+    if (hist_smem_bytes(g, hist_copies, hist_group, walk_code) > 220 * 1024)
         return MCLAHE_ERR_INVALID_ARG;
     if (hist_smem_bytes(g, hist_copies, hist_group) > 220 * 1024) return MCLAHE_ERR_INVALID_ARG;
     p->t.hist_group = hist_group;
@@ -321,7 +323,7 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     p->t.hist_shares = hist_shares;
     p->t.map_chunks = map_chunks;
     p->t.map_tma = map_tma;
-    p->t.hist_tma = hist_tma;
+    p->t.hist_walk = hist_walk;
     p->tuned = 2;
     return MCLAHE_OK;
 }

@@ -130,6 +130,18 @@ def test_set_shapes_validates_and_round_trips(nat):
     odd = nat.mclahe_plan((19, 23, 29), (5, 4, 7), 100, 0.02)
     with pytest.raises(nat.MclaheError):
         nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 1)
+    # histogram row walks: 0 ring, 1 TMA tiles (aligned rows only), 2 per-thread loads
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=2)
+    assert nat.mclahe_plan_query(plan)["hist_walk"] == 2
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=1)
+    assert nat.mclahe_plan_query(plan)["hist_walk"] == 1
+    for bad_walk in (-1, 3):
+        with pytest.raises(nat.MclaheError):
+            nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=bad_walk)
+    nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 0, hist_walk=2)
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 0, hist_walk=1)
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=0)
     info = nat.mclahe_plan_query(plan)   # unchanged by the rejected calls
     assert (info["hist_group"], info["hist_cluster"], info["hist_copies"], info["hist_shares"],
             info["map_chunks"]) == (1, 4, 16, 0, 1)

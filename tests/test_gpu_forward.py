@@ -151,7 +151,8 @@ def test_tma_mapping_matches_oracle(torch_cuda, orc, case, chunks):
     assert nat.mclahe_sync_status(op.ws) == 0
 
 
-# the histogram pass on TMA box tiles: 2- to 4-D, both range modes, cluster and
+# the histogram pass on TMA box tiles and on per-thread loads (the ring walk is
+# the default of every other test): 2- to 4-D, both range modes, cluster and
 # flat forms, mirror pieces that start off a 16-byte boundary
 TMA_HIST_CASES = [
     ((64, 64), (16, 16), 256, 0.02, False),
@@ -166,18 +167,19 @@ TMA_HIST_FORMS = [dict(hist_group=1, hist_cluster=2, hist_copies=4, hist_shares=
                   dict(hist_group=1, hist_cluster=1, hist_copies=16, hist_shares=300)]
 
 
+@pytest.mark.parametrize("walk", [1, 2], ids=["tma", "loads"])
 @pytest.mark.parametrize("form", range(len(TMA_HIST_FORMS)))
 @pytest.mark.parametrize("case", TMA_HIST_CASES,
                          ids=[str(c[0]) + ("A" if c[4] else "G") for c in TMA_HIST_CASES])
-def test_tma_histogram_matches_oracle(torch_cuda, orc, case, form):
+def test_histogram_walks_match_oracle(torch_cuda, orc, case, form, walk):
     from paper_1906_11355_gb300 import _native as nat
 
     shape, ks, nb, clip, adaptive = case
     rng = np.random.default_rng(hash((shape, ks, nb, form, 7)) % 2**32)
     x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
-    shapes = dict(TMA_HIST_FORMS[form], map_chunks=1, hist_tma=1)
+    shapes = dict(TMA_HIST_FORMS[form], map_chunks=1, hist_walk=walk)
     op, _, _ = run_case(torch_cuda, orc, x, ks, nb, clip, adaptive, shapes=shapes)
-    assert op.shapes()["hist_tma"] == 1
+    assert op.shapes()["hist_walk"] == walk
     assert nat.mclahe_sync_status(op.ws) == 0
 
 

@@ -434,7 +434,7 @@ def run_native(args):
     elif not args.no_autotune:
         op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
     shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
-              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk",
+              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk", "hist_threads",
                        "map_chunks", "map_tma", "tuned")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -126,6 +126,8 @@ typedef struct {
     int32_t map_tma;              /* 1: the mapping pass streams its cells as TMA box tiles */
     int32_t hist_walk;            /* rows of the histogram pass: 0 cp.async ring, 1 TMA box
                                      tiles, 2 per-thread loads (least shared memory) */
+    int32_t hist_threads;         /* threads per histogram CTA (256; 512 allowed for 4-D) */
+    int32_t reserved;
 } mclahe_plan_info;
 
 /*
@@ -272,6 +274,7 @@ MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, 
  *                 whose last extent is a multiple of 4, footprint rows of at most 256
  *                 elements per tile); 2: per-thread loads into registers (no row buffer
  *                 in shared memory).
+ *   hist_threads  threads per histogram CTA: 256, or 512 for 4-D volumes.
  *   map_chunks    CTAs per inter-kernel cell in the mapping pass, 1..64.
  *   map_tma       0: per-thread loads and stores; 1: TMA box tiles (3- and 4-D volumes
  *                 whose last dim and cell rows start on 16-byte boundaries only).
@@ -282,7 +285,8 @@ MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, 
 MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist_group,
                                                 int32_t hist_cluster, int32_t hist_copies,
                                                 int32_t hist_shares, int32_t hist_walk,
-                                                int32_t map_chunks, int32_t map_tma);
+                                                int32_t hist_threads, int32_t map_chunks,
+                                                int32_t map_tma);
 
 /* Size of the library's built-in scratch array used by mclahe_forward_noalloc. */
 #define MCLAHE_NOALLOC_SCRATCH_BYTES (8u << 20)

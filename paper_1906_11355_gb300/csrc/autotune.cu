@@ -104,40 +104,42 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
     // the range pass: the flat form's adaptive range is its own pass)
     int64_t item_rows = 1;
     for (int j = 0; j + 1 < p->g.D; ++j) item_rows *= p->g.d[j].b;
-    for (int G : groups) {
-        for (int R = 2; R <= 32 && s == MCLAHE_OK; R <<= 1) {
-            if (hist_smem_bytes(p->g, R, G, 0) > 200 * 1024) continue;
-            p->t.hist_group = G;
-            p->t.hist_copies = R;
-            // cluster form: C CTAs per item; flat form: S shares per item
-            int bx, by;
-            const bool tma_ok = hist_tma_box(p->g, G, bx, by);
-            for (int v = 0; v < (4 + 9) * 3; ++v) {
-                const int f = v % 13;
-                p->t.hist_walk = v / 13;   // ring, TMA tiles, per-thread loads
-                if (p->t.hist_walk == 1 && !tma_ok) continue;
-                const int code = p->t.hist_walk == 0 ? 1 : p->t.hist_walk == 1 ? 2 : 0;
-                if (hist_smem_bytes(p->g, R, G, code) > 200 * 1024) continue;
-                if (f < 4) {
-                    p->t.hist_chunks = 1 << f;
-                    p->t.hist_shares = 0;
-                } else {
-                    p->t.hist_chunks = 1;
-                    p->t.hist_shares = 1 << (f - 4);
-                    if (p->t.hist_shares > item_rows) continue;
-                }
-                const float ms = time_passes(*p, MCLAHE_PASS_CLEAR, MCLAHE_PASS_HIST, d_in, d_out,
-                                             ws, st, e0, e1);
-                if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best.hist_group = G;
-                    best.hist_chunks = p->t.hist_chunks;
-                    best.hist_shares = p->t.hist_shares;
-                    best.hist_copies = R;
-                    best.hist_walk = p->t.hist_walk;
+    // candidates: G x R x threads per CTA (512 only for 4-D) x walk x form
+    struct Cand {
+        int G, R, th, walk, C, S;
+    };
+    std::vector<Cand> cands;
+    for (int G : groups)
+        for (int R = 2; R <= 32; R <<= 1)
+            for (int th = 256; th <= (p->g.D >= 4 ? 512 : 256); th *= 2) {
+                int bx, by;
+                const bool tma_ok = hist_tma_box(p->g, G, bx, by);
+                for (int walk = 0; walk < 3; ++walk) {
+                    if (walk == 1 && !tma_ok) continue;
+                    if (hist_smem_bytes(p->g, R, G, hist_walk_code(walk), th) > 200 * 1024) continue;
+                    for (int C = 1; C <= 8; C <<= 1) cands.push_back({G, R, th, walk, C, 0});
+                    for (int S = 1; S <= 256 && S <= item_rows; S <<= 1)
+                        cands.push_back({G, R, th, walk, 1, S});
                 }
             }
+    for (const Cand &c : cands) {
+        if (s != MCLAHE_OK) break;
+        p->t.hist_group = c.G;
+        p->t.hist_copies = c.R;
+        p->t.hist_threads = c.th;
+        p->t.hist_walk = c.walk;
+        p->t.hist_chunks = c.C;
+        p->t.hist_shares = c.S;
+        const float ms = time_passes(*p, MCLAHE_PASS_CLEAR, MCLAHE_PASS_HIST, d_in, d_out, ws, st, e0, e1);
+        if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
+        if (ms < best_ms) {
+            best_ms = ms;
+            best.hist_group = c.G;
+            best.hist_copies = c.R;
+            best.hist_threads = c.th;
+            best.hist_walk = c.walk;
+            best.hist_chunks = c.C;
+            best.hist_shares = c.S;
         }
     }
     cudaGetLastError();   // clear a failed candidate's launch error

@@ -539,8 +539,14 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     auto walk_full = [&](auto sd_tag, const int *box_lo, const int *len, int r0, int r1,
                          const TileShape &ts, auto &&slot, auto &&quad_full) {
         using SD = typename decltype(sd_tag)::type;
-        walk_tile_async<D, kHistQmax, kHistStages, NoRow, SD, true>(in, stride, box_lo, len, r0, r1, ts,
-                                                                    ring, slot, no_row, quad_full);
+        if constexpr (HW == kHistRing) {
+            walk_tile_async<D, kHistQmax, kHistStages, NoRow, SD, true>(in, stride, box_lo, len, r0, r1,
+                                                                        ts, ring, slot, no_row, quad_full);
+        } else {
+            walk_tile<D, kHistQmax, 4, NoRow, SD, false, false, true>(in, nullptr, stride, box_lo, len, r0,
+                                                                      r1, ts, false, slot, no_row,
+                                                                      quad_full);
+        }
     };
     auto walk = [&](auto sd_tag, const int *box_lo, const int *len, int r0, int r1,
                     const TileShape &ts, auto &&slot, auto &&quad) {
@@ -629,7 +635,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                         }
                     }
                 };
-                if (HW == kHistRing && kgfix >= 0 && whole_quads(len, ts)) {
+                if (HW != kHistTma && kgfix >= 0 && whole_quads(len, ts)) {
                     auto quad_full = [&](NoRow &, const MSlot &, int i, const float4 &v, const float4 &,
                                          int64_t) {
                         mn[i] = min3f(mn[i], v.x, v.y);
@@ -767,7 +773,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                             if (sd.q0 + e >= 0 && sd.q0 + e < L) red_shared_add(bits[e] * r4 + base, wu);
                     }
                 };
-                if (HW == kHistRing && whole_quads(len, ts)) {
+                if (HW != kHistTma && whole_quads(len, ts)) {
                     auto quad_full = [&](NoRow &, const FSlot &, int, const float4 &v, const float4 &,
                                          int64_t) {
                         const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);

@@ -159,12 +159,25 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
     auto add = [&](const BRow &st, float x, float gv, float w1) {
         const float gw1 = gv * w1, gw0 = gv - gw1;
         const float ge = rodd ? gw1 : gw0, go = rodd ? gw0 : gw1;   // even / odd steps
-        const uint32_t gbits = ADAPTIVE ? 0u : qbits1(x, nl[0], sc[0], iqk, qkf);
+        uint32_t bins[NC];
+        if (ADAPTIVE && NC >= 2) {
+            // the corners' bins two at a time (packed; the same roundings as qbits1)
+#pragma unroll
+            for (int t = 0; t < NC; t += 2) {
+                const uint2 b2 = qbits2(make_float2(x, x), make_float2(nl[t], nl[t + 1]),
+                                        make_float2(sc[t], sc[t + 1]), iqk, qkf);
+                bins[t] = b2.x;
+                bins[t + 1] = b2.y;
+            }
+        } else {
+            const uint32_t b0 = qbits1(x, nl[0], sc[0], iqk, qkf);
+#pragma unroll
+            for (int t = 0; t < NC; ++t) bins[t] = b0;
+        }
 #pragma unroll
         for (int t = 0; t < NC; ++t) {
-            const uint32_t b = ADAPTIVE ? qbits1(x, nl[t], sc[t], iqk, qkf) : gbits;
             const float v = st.w[t] * ((t & 1) ? go : ge);
-            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(b * IB + cbase[t]), "f"(v) : "memory");
+            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(bins[t] * IB + cbase[t]), "f"(v) : "memory");
         }
     };
     if ((g.d[D - 1].s & 3) == 0) {
@@ -186,8 +199,21 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
             for (int e = 0; e < 4; ++e)
                 if (sd.e0 + e >= 0 && sd.e0 + e < L) add(st, vals[e], gs[e], fmaf(float(e), two_inv2b, sd.fbi));
         };
-        walk_tile<D, 4, 2, BRow, BSlot, true>(in, gout, stride, box_lo, len, r0, r1, ts, true, slot,
-                                              row_fn, quad);
+        if (ts.head == 0 && ts.QL == 4 && L == 16 * ts.LPR) {
+            // every slot of every row is a whole quad: no per-voxel tests
+            auto quad_full = [&](BRow &st, const BSlot &sd, int, const float4 &v, const float4 &gq,
+                                 int64_t) {
+                add(st, v.x, gq.x, sd.fbi);
+                add(st, v.y, gq.y, fmaf(1.0f, two_inv2b, sd.fbi));
+                add(st, v.z, gq.z, fmaf(2.0f, two_inv2b, sd.fbi));
+                add(st, v.w, gq.w, fmaf(3.0f, two_inv2b, sd.fbi));
+            };
+            walk_tile<D, 4, 2, BRow, BSlot, true, false, true>(in, gout, stride, box_lo, len, r0, r1, ts,
+                                                               true, slot, row_fn, quad_full);
+        } else {
+            walk_tile<D, 4, 2, BRow, BSlot, true>(in, gout, stride, box_lo, len, r0, r1, ts, true, slot,
+                                                  row_fn, quad);
+        }
     } else {
         auto row64 = [&](const int *coords, int64_t, BRow &st) { row_fn(coords, st); };
         auto quad_fn = [&](BRow &st, const QuadRef &q) {

@@ -10,18 +10,18 @@
 
 namespace mclahe {
 
-size_t hist_smem_bytes(const Geom &g, int copies, int group, int walk) {
+size_t hist_smem_bytes(const Geom &g, int copies, int group, int walk, int threads) {
     const size_t words = hist_smem_words(g.P, copies, group);
-    if (walk == kHistRing) return hist_ring_offset_words(words) * sizeof(uint32_t) + hist_ring_bytes(256);
+    if (walk == kHistRing) return hist_ring_offset_words(words) * sizeof(uint32_t) + hist_ring_bytes(threads);
     if (walk == kHistTma) return words * sizeof(uint32_t) + 128 + size_t(kHistTmaStages) * kHistTmaStage;
     return words * sizeof(uint32_t);
 }
 
 // The range pass of the flat form keeps only keys and ranges, plus the walk's buffers.
-size_t hist_range_smem_bytes(int group, int walk) {
+size_t hist_range_smem_bytes(int group, int walk, int threads) {
     const size_t words = 5 * size_t(group);
     if (walk == kHistTma) return words * sizeof(uint32_t) + 128 + size_t(kHistTmaStages) * kHistTmaStage;
-    if (walk == kHistRing) return hist_ring_offset_words(words) * sizeof(uint32_t) + hist_ring_bytes(256);
+    if (walk == kHistRing) return hist_ring_offset_words(words) * sizeof(uint32_t) + hist_ring_bytes(threads);
     return words * sizeof(uint32_t);
 }
 

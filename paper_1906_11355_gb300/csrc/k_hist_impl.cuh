@@ -25,8 +25,10 @@ __device__ __forceinline__ uint32_t hist_tma_stage0(const uint32_t *sh, size_t w
     return (uint32_t(__cvta_generic_to_shared(sh)) + uint32_t(words * 4) + 127u) & ~127u;
 }
 
+// 4-D volumes also run 512-thread CTAs (their lane copies fill the shared
+// memory, so twice the warps per SM share one copy set).
 template <int D, bool ADAPTIVE, int HW>
-__global__ void __launch_bounds__(256, (D >= 4 || HW == kHistTma) ? 2 : 3)
+__global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistTma ? 2 : 3))
     k_hist(Geom g, const __grid_constant__ CUtensorMap tmap, int tbx, int tby,
            const float *__restrict__ in, const uint32_t *__restrict__ keys,
            const float *__restrict__ d_clip, uint32_t *__restrict__ hist, float *__restrict__ lut,
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(256, (D >= 4 || HW == kHistTma) ? 2 : 3)
 // Flat forms: CTA b takes shares [total * b / grid, total * (b + 1) / grid)
 // of the work items' S shares each, item by item.
 template <int D, bool ADAPTIVE, int MODE, int HW>
-__global__ void __launch_bounds__(256, (D >= 4 || HW == kHistTma) ? 2 : 3)
+__global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistTma ? 2 : 3))
     k_hist_flat(Geom g, const __grid_constant__ CUtensorMap tmap, int tbx, int tby,
                 const float *__restrict__ in, const uint32_t *__restrict__ keys,
                 const float *__restrict__ d_clip, uint32_t *__restrict__ hist,
@@ -88,7 +90,7 @@ static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const float *in, 
                                        const float *d_clip, cudaStream_t st, const HistTmaArgs &ta) {
     const Geom &g = p.g;
     const int C = p.t.hist_chunks;
-    const size_t smem = hist_smem_bytes(g, p.t.hist_copies, p.t.hist_group, HW);
+    const size_t smem = hist_smem_bytes(g, p.t.hist_copies, p.t.hist_group, HW, p.t.hist_threads);
     auto kern = k_hist<D, ADAPTIVE, HW>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), size_t(smem));
     if (e != cudaSuccess) return e;
@@ -120,7 +122,8 @@ static cudaError_t launch_hist_flat(const mclahe_plan_s &p, const float *in, uns
                                     const float *d_clip, cudaStream_t st, const HistTmaArgs &ta) {
     const Geom &g = p.g;
     const int G = p.t.hist_group, R = p.t.hist_copies, S = p.t.hist_shares;
-    const size_t smem = MODE == kHistMinMax ? hist_range_smem_bytes(G, HW) : hist_smem_bytes(g, R, G, HW);
+    const size_t smem = MODE == kHistMinMax ? hist_range_smem_bytes(G, HW, p.t.hist_threads)
+                                            : hist_smem_bytes(g, R, G, HW, p.t.hist_threads);
     auto kern = k_hist_flat<D, ADAPTIVE, MODE, HW>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), size_t(smem));
     if (e != cudaSuccess) return e;

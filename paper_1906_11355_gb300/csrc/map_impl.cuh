@@ -612,6 +612,16 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                 walk_tile_async<D, QM, kMapStages, MRow, MSlot>(in, stride, box_lo, len, r0, r1, ts, ring,
                                                                  slot, row2, quad);
             }
+        } else if (ts.head == 0 && ts.QL == QM && L == 4 * ts.LPR * QM) {
+            auto quad_full = [&](MRow &st, const MSlot &sd, int, const float4 &v, const float4 &,
+                                 int64_t a) {
+                const float vals[4] = {v.x, v.y, v.z, v.w};
+                float res[4];
+                map4(st, vals, sd.fbi, res);
+                __stcs(reinterpret_cast<float4 *>(out + a), make_float4(res[0], res[1], res[2], res[3]));
+            };
+            walk_tile<D, QM, 4, MRow, MSlot, false, false, true>(in, nullptr, stride, box_lo, len, r0, r1,
+                                                                 ts, true, slot, row2, quad_full);
         } else {
             walk_tile<D, QM, 4, MRow, MSlot, false>(in, nullptr, stride, box_lo, len, r0, r1, ts, true,
                                                     slot, row2, quad);

@@ -72,7 +72,7 @@ struct Geom {
 
 // Launch shapes chosen by the heuristic or the autotuner.
 struct Tuning {
-    int hist_threads;   // threads per histogram CTA
+    int hist_threads;   // threads per histogram CTA (256; 512 for 4-D volumes)
     int hist_chunks;    // CTAs per kernel (cluster size) in the histogram pass
     int hist_copies;    // lane copies of the shared-memory histograms (1 .. 32)
     int hist_group;     // kernels along the last dimension per histogram work item
@@ -522,8 +522,10 @@ __device__ __forceinline__ TileShape tile_shape(int L, int head, int nthreads, i
     return t;
 }
 
+// FULL: every slot of every row is a whole quad inside the box (checked by the
+// caller): no per-slot tests.
 template <int D, int QMAX, int U, typename S, typename SD, bool TWO, bool PF = false,
-          typename SlotFn, typename RowFn, typename QuadFn>
+          bool FULL = false, typename SlotFn, typename RowFn, typename QuadFn>
 __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
                                           const float *__restrict__ in2, const int64_t *stride,
                                           const int *box_lo, const int *box_len, int r0, int r1,
@@ -557,7 +559,7 @@ __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
     auto load = [&](int64_t a0, int i0, float4 (&v)[U], float4 (&v2)[U]) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            if (ok[i0 + u]) {
+            if (FULL || ok[i0 + u]) {
                 const float4 *q = reinterpret_cast<const float4 *>(in + a0 + (i0 + u) * step);
                 v[u] = stream ? __ldcs(q) : __ldg(q);
                 if (TWO) v2[u] = __ldcs(reinterpret_cast<const float4 *>(in2 + a0 + (i0 + u) * step));
@@ -587,7 +589,7 @@ __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
             row_fn(cc, st);
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (ok[u]) quad_fn(st, sd[u], u, v[u], v2[u], ac + u * step);
+                if (FULL || ok[u]) quad_fn(st, sd[u], u, v[u], v2[u], ac + u * step);
             if (rn >= r1) break;
             r = rn;
             ac = an;
@@ -614,7 +616,7 @@ __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
                 load(a0, i0, v, v2);
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (ok[i0 + u]) quad_fn(st, sd[i0 + u], i0 + u, v[u], v2[u], a0 + (i0 + u) * step);
+                    if (FULL || ok[i0 + u]) quad_fn(st, sd[i0 + u], i0 + u, v[u], v2[u], a0 + (i0 + u) * step);
             }
         }
     }
@@ -753,8 +755,11 @@ size_t bwd_partial_floats(const Geom &g, int chunks);
 // Dynamic shared memory of a histogram CTA for a row walk (0: per-thread
 // loads, the batched launch; 1: the cp.async row ring; 2: TMA tiles), and of
 // the flat form's range pass.
-size_t hist_smem_bytes(const Geom &g, int copies, int group, int walk = 1);
-size_t hist_range_smem_bytes(int group, int walk);
+size_t hist_smem_bytes(const Geom &g, int copies, int group, int walk = 1, int threads = 256);
+size_t hist_range_smem_bytes(int group, int walk, int threads);
+// the row-walk code of hist_smem_bytes for a plan's hist_walk (0 ring, 1 TMA tiles,
+// 2 per-thread loads)
+inline int hist_walk_code(int hist_walk) { return hist_walk == 0 ? 1 : hist_walk == 1 ? 2 : 0; }
 bool hist_tma_box(const Geom &g, int group, int &bx, int &by);
 // Tensor map of a float32 volume (dims innermost first) with box[0..D-1]
 // elements per tile (tma_host.cu).

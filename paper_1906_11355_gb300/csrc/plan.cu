@@ -48,7 +48,7 @@ int64_t n_cells(const Geom &g) {
 //   keeps some thousands of voxels.
 Tuning default_tuning(const Geom &g) {
     Tuning t;
-    t.hist_threads = 256;
+    t.hist_threads = 256;   // 512 for 4-D below, with the whole-row group
     t.map_threads = 256;
     const Dim &dl = g.d[g.D - 1];
     int G = std::min(dl.n, std::max(1, (64 + dl.b - 1) / dl.b));
@@ -59,6 +59,7 @@ Tuning default_tuning(const Geom &g) {
     while (G > 1 && hist_smem_bytes(g, R, G, false) > 100 * 1024) G >>= 1;
     t.hist_group = G;
     t.hist_copies = R;
+    if (g.D >= 4 && hist_smem_bytes(g, R, G, 1, 512) <= 220 * 1024) t.hist_threads = 512;
     const int sms = 152;
     const int64_t vitem = g.V * G, items = hist_items(g, G);
     int C = 1;
@@ -290,6 +291,7 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->hist_ctas = p->t.hist_shares > 0 ? p->flat_ctas : 0;
     info->map_tma = p->t.map_tma;
     info->hist_walk = p->t.hist_walk;
+    info->hist_threads = p->t.hist_threads;
     info->hist_copies = p->t.hist_copies;
     info->map_chunks = p->t.map_chunks;
     info->bwd_chunks = p->t.bwd_chunks;
@@ -299,7 +301,7 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
 
 mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_t hist_cluster,
                                      int32_t hist_copies, int32_t hist_shares, int32_t hist_walk,
-                                     int32_t map_chunks, int32_t map_tma) {
+                                     int32_t hist_threads, int32_t map_chunks, int32_t map_tma) {
     if (!p) return MCLAHE_ERR_INVALID_ARG;
     auto pow2 = [](int32_t v, int32_t hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
     const Geom &g = p->g;
@@ -312,11 +314,9 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     if (map_tma != 0 && (map_tma != 1 || !map_tma_box(g, bx, by, bz))) return MCLAHE_ERR_INVALID_ARG;
     if (hist_walk < 0 || hist_walk > 2 || (hist_walk == 1 && !hist_tma_box(g, hist_group, bx, by)))
         return MCLAHE_ERR_INVALID_ARG;
-    // walk codes of hist_smem_bytes: 1 ring, 2 TMA, 0 per-thread loads
-    const int walk_code = hist_walk == 0 ? 1 : hist_walk == 1 ? 2 : 0;
-    if (hist_smem_bytes(g, hist_copies, hist_group, walk_code) > 220 * 1024)
+    if (hist_threads != 256 && !(hist_threads == 512 && g.D >= 4)) return MCLAHE_ERR_INVALID_ARG;
+    if (hist_smem_bytes(g, hist_copies, hist_group, hist_walk_code(hist_walk), hist_threads) > 220 * 1024)
         return MCLAHE_ERR_INVALID_ARG;
-    if (hist_smem_bytes(g, hist_copies, hist_group) > 220 * 1024) return MCLAHE_ERR_INVALID_ARG;
     p->t.hist_group = hist_group;
     p->t.hist_chunks = hist_cluster;
     p->t.hist_copies = hist_copies;
@@ -324,6 +324,7 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     p->t.map_chunks = map_chunks;
     p->t.map_tma = map_tma;
     p->t.hist_walk = hist_walk;
+    p->t.hist_threads = hist_threads;
     p->tuned = 2;
     return MCLAHE_OK;
 }

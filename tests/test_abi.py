@@ -142,6 +142,14 @@ def test_set_shapes_validates_and_round_trips(nat):
     with pytest.raises(nat.MclaheError):
         nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 0, hist_walk=1)
     nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=0)
+    # 512-thread histogram CTAs only for 4-D volumes
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_threads=512)
+    p4 = nat.mclahe_plan((16, 16, 24, 8), (4, 4, 6, 2), 256, 0.01)
+    nat.mclahe_plan_set_shapes(p4, 1, 1, 8, 0, 1, 0, hist_threads=512)
+    assert nat.mclahe_plan_query(p4)["hist_threads"] == 512
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_plan_set_shapes(p4, 1, 1, 8, 0, 1, 0, hist_threads=384)
     info = nat.mclahe_plan_query(plan)   # unchanged by the rejected calls
     assert (info["hist_group"], info["hist_cluster"], info["hist_copies"], info["hist_shares"],
             info["map_chunks"]) == (1, 4, 16, 0, 1)

@@ -223,10 +223,13 @@ MCLAHE_API int mclahe_pass_launches(mclahe_plan_t plan, mclahe_pass pass);
  *   d_in, d_ws    as passed to the mclahe_forward call being differentiated
  *                 (the workspace must still hold that call's range and
  *                 histograms).
- *   d_grad_out    device, prod(shape) float32.
+ *   d_grad_out    device, prod(shape) float32, finite.
  *   d_clip        the same clip pointer as the forward call (nullable).
  *   d_grad_lut    nullable device float [K][n_bins]: receives dL/dlut.
  *   d_grad_clip   device float scalar: receives dL/dclip_limit.
+ * The per-voxel terms g_v * c_i(v) are summed as fixed-point integers (each
+ * rounded at a scale set by max |g|, relative resolution 2^-30 of it), so the
+ * results are deterministic; the plan requires kernel_size[D-1] <= 65535.
  */
 MCLAHE_API mclahe_status mclahe_backward(mclahe_plan_t plan, const float *d_in, const float *d_grad_out,
                               void *d_ws, size_t ws_bytes, const float *d_clip, float *d_grad_lut,

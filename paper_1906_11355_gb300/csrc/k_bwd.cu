@@ -7,11 +7,19 @@
 //   dL/dlut[k][j] = sum over voxels v and corners i with k0(v) + i = k and
 //                   bin_k(v) = j of g_v * c_i(v).
 // Three launches:
+//   k_gmax    the largest |g| of the upstream gradient (the fixed-point scale);
 //   k_adj     one CTA per chunk of an inter-kernel cell: streams the input and
 //             the upstream gradient, accumulates g * c_i into the cell's 2^D
-//             corner tables in shared memory (float reductions, lane-rotated
-//             copies: conflict-free whatever the bins) and writes them, copies
-//             summed, as the chunk's partial table gradients;
+//             corner tables in shared memory and writes them, copies summed,
+//             as the chunk's partial table gradients.  The sums are exact
+//             integers: each term is rounded to a fixed-point integer f with
+//             |f| < 2^30 (scale 2^E from max |g|) and added as two 32-bit
+//             words, hi = f >> 15 and lo = f & 0x7fff, into separate
+//             accumulators (32-bit integer shared-memory reductions run several
+//             times faster than float ones, and the result does not depend on
+//             the order); with at most 65535 voxels per chunk neither word's
+//             sum can overflow.  Lane-rotated copies keep the reductions
+//             conflict-free whatever the bins;
 //   k_lutbwd  one CTA per kernel: sums the partials of the cells around the
 //             kernel in a fixed order (deterministic), folds the padded table
 //             indices, stores dL/dlut, and takes the reverse of clip,
@@ -23,6 +31,8 @@
 //   k_clipgrad one CTA: dL/dclip = V * sum_k dL/dT_k in a fixed order (0 when
 //             the clip limit given lies outside [0, 1], where the forward
 //             clamps it).
+#include <algorithm>
+
 #include "hist_impl.cuh"
 #include "map_impl.cuh"   // rotate_left
 
@@ -34,8 +44,36 @@ namespace mclahe {
 // banks (the index is shared or not); the lane rotation is undone by rotated
 // per-lane weights and ranges, as in the mapping pass.  Plain: [corner][index].
 __host__ __device__ inline bool adj_repl(int P) { return size_t(P) * 128 <= 160 * 1024; }
-__host__ __device__ inline size_t adj_smem(int D, int P) {
-    return adj_repl(P) ? size_t(P) * 128 : (size_t(1) << D) * size_t(P) * sizeof(float);
+// bytes of one accumulator array (hi or lo words)
+__host__ __device__ inline size_t adj_words_bytes(int D, int P) {
+    return adj_repl(P) ? size_t(P) * 128 : (size_t(1) << D) * size_t(P) * sizeof(uint32_t);
+}
+__host__ __device__ inline size_t adj_smem(int D, int P) { return 2 * adj_words_bytes(D, P); }
+
+// Fixed-point exponent E of a launch: max|g| * 2^E < 2^30 (0 if g is all zero).
+__device__ __forceinline__ int adj_exponent(uint32_t gmax_key) {
+    const float gmax = __uint_as_float(gmax_key);
+    if (!(gmax > 0.0f)) return 0;
+    int e;
+    frexpf(gmax, &e);   // gmax < 2^e
+    return min(max(30 - e, -126), 126);
+}
+
+// the largest |g| as an order-preserving key (|g| as bits: non-negative floats
+// order as unsigned integers)
+__global__ void __launch_bounds__(256) k_gmax(const float *__restrict__ g, int64_t n,
+                                              uint32_t *__restrict__ key) {
+    float m = 0.0f;
+    const int64_t nq = n >> 2;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const float4 v = __ldcs(reinterpret_cast<const float4 *>(g) + q);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int64_t t = (nq << 2) + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += stride)
+        m = fmaxf(m, fabsf(g[t]));
+    const uint32_t k = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) atomicMax(key, k);
 }
 
 template <int D, bool ADAPTIVE, bool REPL>
@@ -43,11 +81,12 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
                                                 const float *__restrict__ gout,
                                                 const float *__restrict__ lo_k,
                                                 const float *__restrict__ scale_k,
-                                                float *__restrict__ part, int chunks) {
+                                                float *__restrict__ part, int chunks,
+                                                const uint32_t *__restrict__ gmax_key) {
     constexpr int NC = 1 << D;
     constexpr int NO = 1 << (D - 1);
     constexpr int RC = REPL ? 32 / NC : 1;      // copies
-    extern __shared__ __align__(16) float acc[];
+    extern __shared__ __align__(16) uint32_t acc[];   // hi words, then lo words
     __shared__ float s_nlo[NC], s_sc[NC];
     const int P = g.P, LS = g.LS;
     const int lane = threadIdx.x & 31;
@@ -74,10 +113,10 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
         }
     }
     {
-        float4 *z = reinterpret_cast<float4 *>(acc);
-        const int n4 = int(NC * P * RC / 4);
-        for (int i = threadIdx.x; i < n4; i += blockDim.x) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int i = n4 * 4 + threadIdx.x; i < NC * P * RC; i += blockDim.x) acc[i] = 0.0f;
+        uint4 *z = reinterpret_cast<uint4 *>(acc);
+        const int n4 = int(2 * NC * P * RC / 4);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = n4 * 4 + threadIdx.x; i < 2 * NC * P * RC; i += blockDim.x) acc[i] = 0u;
     }
     if (threadIdx.x < NC) {
         int64_t k = kbase;
@@ -112,6 +151,9 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
         mb[j] = 2 * dj.p0 - (dj.b - 1) - 2 * dj.b * cc[j];
     }
     const uint32_t acc_s = uint32_t(__cvta_generic_to_shared(acc));
+    const uint32_t lo_off = uint32_t(NC * P * RC) * 4u;   // the lo words behind the hi words
+    const int E = adj_exponent(__ldcg(gmax_key));
+    const float fscale = ldexpf(1.0f, E);
     const float iqk = g.iqk, qkf = g.qkf;
     const int rot = REPL ? (lane & (NC - 1)) : 0;
     const int copy = REPL ? (lane / NC) : 0;
@@ -177,7 +219,11 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
 #pragma unroll
         for (int t = 0; t < NC; ++t) {
             const float v = st.w[t] * ((t & 1) ? go : ge);
-            asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(bins[t] * IB + cbase[t]), "f"(v) : "memory");
+            const int f = __float2int_rn(v * fscale);   // |f| < 2^30
+            const uint32_t a = bins[t] * IB + cbase[t];
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(uint32_t(f >> 15)) : "memory");
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a + lo_off), "r"(uint32_t(f & 0x7fff))
+                         : "memory");
         }
     };
     if ((g.d[D - 1].s & 3) == 0) {
@@ -229,17 +275,21 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
                                    quad_fn);
     }
     __syncthreads();
-    // the chunk's partial table gradients, copies summed
+    // the chunk's partial table gradients, copies summed: exact integers,
+    // one rounding to float, then the scale
     float *dst = part + (cell * chunks + chunk) * NC * LS;
+    const float inv = ldexpf(1.0f, -E);
     for (int i = threadIdx.x; i < NC * LS; i += blockDim.x) {
         const int c = i / LS, j = i - c * LS;
-        float v = 0.0f;
+        int64_t tot = 0;
         if (j < P) {
-            const float *a = acc + (size_t(c) * P + j) * RC;
+            const uint32_t *hi = acc + (size_t(c) * P + j) * RC;
+            const uint32_t *lo = hi + NC * P * RC;
 #pragma unroll
-            for (int q = 0; q < RC; ++q) v += a[q];
+            for (int q = 0; q < RC; ++q)
+                tot += int64_t(int32_t(hi[q])) * 32768 + int64_t(lo[q]);
         }
-        dst[i] = v;
+        dst[i] = float(tot) * inv;
     }
 }
 
@@ -353,16 +403,24 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
     const int chunks = p.t.bwd_chunks;
     float *part = reinterpret_cast<float *>(ws + p.ws.scratch);
     float *dT = part + bwd_partial_floats(g, chunks);
+    uint32_t *gmax_key = reinterpret_cast<uint32_t *>(dT + g.K);
     const size_t smem_adj = adj_smem(D, g.P);
     const unsigned grid = unsigned(n_cells(g) * chunks);
     const bool repl = adj_repl(g.P);
     const float *lo = reinterpret_cast<const float *>(ws + p.ws.lo);
     const float *sc = reinterpret_cast<const float *>(ws + p.ws.scale);
-    cudaError_t e;
+    cudaError_t e = cudaMemsetAsync(gmax_key, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    {
+        const int64_t nq = (g.N >> 2) + 1;
+        const int blocks = int(std::min<int64_t>((nq + 255) / 256, int64_t(device_sms()) * 4));
+        k_gmax<<<blocks, 256, 0, st>>>(gout, g.N, gmax_key);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
 #define MCLAHE_ADJ(A, R)                                                                       \
     e = ensure_smem(reinterpret_cast<const void *>(k_adj<D, A, R>), size_t(smem_adj));          \
     if (e != cudaSuccess) return e;                                                            \
-    k_adj<D, A, R><<<grid, 256, smem_adj, st>>>(g, in, gout, lo, sc, part, chunks);
+    k_adj<D, A, R><<<grid, 256, smem_adj, st>>>(g, in, gout, lo, sc, part, chunks, gmax_key);
     if (g.mode == MCLAHE_RANGE_ADAPTIVE) {
         if (repl) { MCLAHE_ADJ(true, true) } else { MCLAHE_ADJ(true, false) }
     } else {

@@ -88,7 +88,13 @@ Tuning default_tuning(const Geom &g) {
     t.hist_walk = 0;
     int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
-    t.bwd_chunks = int(std::min<int64_t>(bc, 32));
+    bc = std::min<int64_t>(bc, 32);
+    // the adjoint's integer accumulators hold at most 65535 voxels per chunk:
+    // ceil(rows / chunks) rows of b_last voxels (b_last <= 65535, checked by
+    // mclahe_plan)
+    const int64_t rows_max = std::max<int64_t>(65535 / dl.b, 1);
+    bc = std::max<int64_t>(bc, (rows + rows_max - 1) / rows_max);
+    t.bwd_chunks = int(bc);
     return t;
 }
 
@@ -114,7 +120,9 @@ Layout make_layout(const Geom &g, const Tuning &t) {
     // backward: partial table gradients (2^D corner tables per cell chunk)
     // and per-kernel threshold gradients
     L.scratch = off;
-    L.scratch_bytes = sizeof(float) * bwd_partial_floats(g, t.bwd_chunks) + sizeof(float) * size_t(g.K);
+    // partials, dL/dT per kernel, the max |g| key of the adjoint's fixed point
+    L.scratch_bytes = sizeof(float) * bwd_partial_floats(g, t.bwd_chunks) + sizeof(float) * size_t(g.K) +
+                      sizeof(uint32_t);
     off = align_up(off + L.scratch_bytes);
     L.total = off;
     return L;
@@ -204,6 +212,7 @@ mclahe_status mclahe_plan(mclahe_plan_t *out, int ndim, const int64_t *shape,
         const int64_t s = shape[j], b = kernel_size[j];
         if (s < 1 || b < 1 || b > s) return MCLAHE_ERR_INVALID_ARG;
         if (s > (int64_t(1) << 30)) return MCLAHE_ERR_UNSUPPORTED;
+        if (j == ndim - 1 && b > 65535) return MCLAHE_ERR_UNSUPPORTED;   // backward chunks
         const int64_t p = 2 * b - 1 - ((s - 1) % b);   // Eq. (1)
         Dim &d = g.d[j];
         d.s = int32_t(s);

@@ -151,3 +151,35 @@ def test_backward_is_deterministic_and_clamped_clip_has_zero_gradient(torch_cuda
     torch.cuda.synchronize()
     assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
     assert res[2][0].item() == 0.0
+
+
+def test_backward_integer_sums_are_deterministic_and_scale_free(torch_cuda):
+    """The adjoint sums fixed-point integers at a scale set by max |g|: repeated
+    calls agree bit for bit, and scaling g by powers of two (far below and far
+    above 1) scales the gradients by exactly the same power of two."""
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    rng = np.random.default_rng(77)
+    shape, ks, nb = (16, 64, 64), (4, 16, 16), 256
+    x = torch.from_numpy(rng.gamma(2.0, 1.0, size=shape).astype(np.float32)).cuda()
+    g = torch.from_numpy(rng.normal(size=shape).astype(np.float32)).cuda()
+    op = MCLAHE(shape, ks, nb, f32(0.02), adaptive=True)
+    op.forward(x)
+
+    def run(gg):
+        gl = torch.empty(op.n_kernels * nb, device="cuda")
+        gc = torch.empty(1, device="cuda")
+        nat.mclahe_backward(op.plan, x, gg, op.ws, op.ws_bytes, None, gl, gc)
+        return gl, gc
+
+    a = run(g)
+    b = run(g)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    for p in (-60, 60):
+        s = run(g * 2.0 ** p)
+        torch.cuda.synchronize()
+        assert torch.equal(s[0], a[0] * 2.0 ** p), p
+        assert torch.equal(s[1], a[1] * 2.0 ** p), p

@@ -10,9 +10,11 @@
 //   k_gmax    the largest |g| of the upstream gradient (the fixed-point scale);
 //   k_adj     one CTA per chunk of an inter-kernel cell: streams the input and
 //             the upstream gradient, accumulates g * c_i into the cell's 2^D
-//             corner tables in shared memory and writes them, copies summed,
-//             as the chunk's partial table gradients.  The sums are exact
-//             integers: each term is rounded to a fixed-point integer f with
+//             corner tables in shared memory and adds them, copies summed, to
+//             the cell's table-gradient sums in global memory (64-bit integer
+//             atomics: exact, so the order of the chunks does not matter).
+//             The sums are exact integers: each term is rounded to a
+//             fixed-point integer f with
 //             |f| < 2^30 (scale 2^E from max |g|) and added as two 32-bit
 //             words, hi = f >> 15 and lo = f & 0x7fff, into separate
 //             accumulators (32-bit integer shared-memory reductions run several
@@ -20,9 +22,9 @@
 //             the order); with at most 65535 voxels per chunk neither word's
 //             sum can overflow.  Lane-rotated copies keep the reductions
 //             conflict-free whatever the bins;
-//   k_lutbwd  one CTA per kernel: sums the partials of the cells around the
-//             kernel in a fixed order (deterministic), folds the padded table
-//             indices, stores dL/dlut, and takes the reverse of clip,
+//   k_lutbwd  one CTA per kernel: sums the integer sums of the cells around
+//             the kernel (exact), scales them to float once, folds the padded
+//             table indices, stores dL/dlut, and takes the reverse of clip,
 //             redistribute, cumulative sum and normalisation:
 //               dL/dT = (1/den) [sum_j g_j (A_j - A_0 - j N_c/nb)
 //                                + (A_0 - N_c/nb) sum_j g_j lut_j],
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
                                                 const float *__restrict__ gout,
                                                 const float *__restrict__ lo_k,
                                                 const float *__restrict__ scale_k,
-                                                float *__restrict__ part, int chunks,
+                                                unsigned long long *__restrict__ sums, int chunks,
                                                 const uint32_t *__restrict__ gmax_key) {
     constexpr int NC = 1 << D;
     constexpr int NO = 1 << (D - 1);
@@ -275,21 +277,16 @@ __global__ void __launch_bounds__(256, 2) k_adj(Geom g, const float *__restrict_
                                    quad_fn);
     }
     __syncthreads();
-    // the chunk's partial table gradients, copies summed: exact integers,
-    // one rounding to float, then the scale
-    float *dst = part + (cell * chunks + chunk) * NC * LS;
-    const float inv = ldexpf(1.0f, -E);
-    for (int i = threadIdx.x; i < NC * LS; i += blockDim.x) {
-        const int c = i / LS, j = i - c * LS;
+    // the chunk's sums, copies summed, added to the cell's integer sums
+    unsigned long long *dst = sums + size_t(cell) * NC * LS;
+    for (int i = threadIdx.x; i < NC * P; i += blockDim.x) {
+        const int c = i / P, j = i - c * P;
+        const uint32_t *hi = acc + (size_t(c) * P + j) * RC;
+        const uint32_t *lo = hi + NC * P * RC;
         int64_t tot = 0;
-        if (j < P) {
-            const uint32_t *hi = acc + (size_t(c) * P + j) * RC;
-            const uint32_t *lo = hi + NC * P * RC;
 #pragma unroll
-            for (int q = 0; q < RC; ++q)
-                tot += int64_t(int32_t(hi[q])) * 32768 + int64_t(lo[q]);
-        }
-        dst[i] = float(tot) * inv;
+        for (int q = 0; q < RC; ++q) tot += int64_t(int32_t(hi[q])) * 32768 + int64_t(lo[q]);
+        if (tot != 0) atomicAdd(dst + size_t(c) * LS + j, static_cast<unsigned long long>(tot));
     }
 }
 
@@ -312,7 +309,8 @@ __device__ __forceinline__ float block_sum(float v) {
 template <int D>
 __global__ void __launch_bounds__(256) k_lutbwd(Geom g, const uint32_t *__restrict__ hist,
                                                 const float *__restrict__ lut,
-                                                const float *__restrict__ part, int chunks,
+                                                const unsigned long long *__restrict__ sums,
+                                                const uint32_t *__restrict__ gmax_key,
                                                 const float *__restrict__ d_clip,
                                                 float *__restrict__ d_grad_lut,
                                                 float *__restrict__ dT) {
@@ -344,15 +342,15 @@ __global__ void __launch_bounds__(256) k_lutbwd(Geom g, const uint32_t *__restri
         }
         cell_of[c] = ok ? cell : -1;
     }
+    // dL/dlut: the integer sums of the (up to 2^D) cells around the kernel,
+    // added exactly, then scaled to float once
+    const float inv = ldexpf(1.0f, -adj_exponent(__ldcg(gmax_key)));
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        float s = 0.0f;
+        int64_t t = 0;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            if (cell_of[c] < 0) continue;
-            const float *p = part + (cell_of[c] * chunks * NC + c) * LS + j;
-            for (int ch = 0; ch < chunks; ++ch) s += p[int64_t(ch) * NC * LS];
-        }
-        G[j] = s;
+        for (int c = 0; c < NC; ++c)
+            if (cell_of[c] >= 0) t += int64_t(__ldcg(sums + (cell_of[c] * NC + c) * LS + j));
+        G[j] = float(t) * inv;
     }
     for (int j = threadIdx.x; j < nb; j += blockDim.x) h[j] = hist[k * nb + j];
     __syncthreads();
@@ -391,8 +389,9 @@ __global__ void __launch_bounds__(256) k_clipgrad(const float *__restrict__ dT, 
     }
 }
 
-size_t bwd_partial_floats(const Geom &g, int chunks) {
-    return size_t(n_cells(g)) * size_t(chunks) * (size_t(1) << g.D) * size_t(g.LS);
+size_t bwd_sum_words(const Geom &g) { return size_t(n_cells(g)) * (size_t(1) << g.D) * size_t(g.LS); }
+size_t bwd_scratch_bytes(const Geom &g) {
+    return 8 * bwd_sum_words(g) + 16 + sizeof(float) * size_t(g.K);
 }
 
 template <int D>
@@ -401,15 +400,16 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
                                 float *d_grad_clip, cudaStream_t st) {
     const Geom &g = p.g;
     const int chunks = p.t.bwd_chunks;
-    float *part = reinterpret_cast<float *>(ws + p.ws.scratch);
-    float *dT = part + bwd_partial_floats(g, chunks);
-    uint32_t *gmax_key = reinterpret_cast<uint32_t *>(dT + g.K);
+    // scratch: integer sums, the max |g| key (cleared together), dL/dT
+    unsigned long long *sums = reinterpret_cast<unsigned long long *>(ws + p.ws.scratch);
+    uint32_t *gmax_key = reinterpret_cast<uint32_t *>(sums + bwd_sum_words(g));
+    float *dT = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(gmax_key) + 16);
     const size_t smem_adj = adj_smem(D, g.P);
     const unsigned grid = unsigned(n_cells(g) * chunks);
     const bool repl = adj_repl(g.P);
     const float *lo = reinterpret_cast<const float *>(ws + p.ws.lo);
     const float *sc = reinterpret_cast<const float *>(ws + p.ws.scale);
-    cudaError_t e = cudaMemsetAsync(gmax_key, 0, sizeof(uint32_t), st);
+    cudaError_t e = cudaMemsetAsync(sums, 0, 8 * bwd_sum_words(g) + sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     {
         const int64_t nq = (g.N >> 2) + 1;
@@ -420,7 +420,7 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
 #define MCLAHE_ADJ(A, R)                                                                       \
     e = ensure_smem(reinterpret_cast<const void *>(k_adj<D, A, R>), size_t(smem_adj));          \
     if (e != cudaSuccess) return e;                                                            \
-    k_adj<D, A, R><<<grid, 256, smem_adj, st>>>(g, in, gout, lo, sc, part, chunks, gmax_key);
+    k_adj<D, A, R><<<grid, 256, smem_adj, st>>>(g, in, gout, lo, sc, sums, chunks, gmax_key);
     if (g.mode == MCLAHE_RANGE_ADAPTIVE) {
         if (repl) { MCLAHE_ADJ(true, true) } else { MCLAHE_ADJ(true, false) }
     } else {
@@ -433,7 +433,7 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
     if (e != cudaSuccess) return e;
     k_lutbwd<D><<<unsigned(g.K), 256, smem_lb, st>>>(
         g, reinterpret_cast<const uint32_t *>(ws + p.ws.hist), reinterpret_cast<const float *>(ws + p.ws.lut),
-        part, chunks, d_clip, d_grad_lut, dT);
+        sums, gmax_key, d_clip, d_grad_lut, dT);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (d_grad_clip) {
         k_clipgrad<<<1, 256, 0, st>>>(dT, g.K, g.V, d_clip, g.clip, d_grad_clip);

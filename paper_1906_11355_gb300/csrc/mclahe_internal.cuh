@@ -751,7 +751,10 @@ cudaError_t launch_map(const mclahe_plan_s &p, const float *in, float *out,
 cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float *gout,
                             unsigned char *ws, const float *d_clip, float *d_grad_lut,
                             float *d_grad_clip, cudaStream_t st);
-size_t bwd_partial_floats(const Geom &g, int chunks);
+// backward scratch: int64 table-gradient sums [cells][2^D][LS], the max |g|
+// key (and padding), dL/dT[K]
+size_t bwd_sum_words(const Geom &g);
+size_t bwd_scratch_bytes(const Geom &g);
 // Dynamic shared memory of a histogram CTA for a row walk (0: per-thread
 // loads, the batched launch; 1: the cp.async row ring; 2: TMA tiles), and of
 // the flat form's range pass.

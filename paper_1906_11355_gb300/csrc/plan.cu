@@ -120,9 +120,7 @@ Layout make_layout(const Geom &g, const Tuning &t) {
     // backward: partial table gradients (2^D corner tables per cell chunk)
     // and per-kernel threshold gradients
     L.scratch = off;
-    // partials, dL/dT per kernel, the max |g| key of the adjoint's fixed point
-    L.scratch_bytes = sizeof(float) * bwd_partial_floats(g, t.bwd_chunks) + sizeof(float) * size_t(g.K) +
-                      sizeof(uint32_t);
+    L.scratch_bytes = bwd_scratch_bytes(g);
     off = align_up(off + L.scratch_bytes);
     L.total = off;
     return L;

@@ -51,6 +51,8 @@ def _load():
         i64p = ctypes.POINTER(ctypes.c_int64)
         vp = ctypes.c_void_p
         lib.orc_geometry.argtypes = [ctypes.c_int, i64p, i64p, i64p, i64p, i64p, i64p]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = None
         lib.orc_pad.argtypes = [ctypes.c_int, i64p, i64p, vp, vp]
         lib.orc_scale.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int]
         lib.orc_scale.restype = ctypes.c_float
@@ -162,6 +164,11 @@ def map_volume(x, ksize, lut, lo, scale_):
     if rc:
         raise ValueError("orc_map failed")
     return out
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops (n < 1: all processors); timing only."""
+    _load().orc_set_threads(int(n))
 
 
 def mclahe(x, ksize, n_bins, clip_limit, mode=GLOBAL, range_=None, full=False):

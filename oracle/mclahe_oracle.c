@@ -38,6 +38,11 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <omp.h>
+
+/* Threads of the OpenMP loops below (n < 1: all processors); timing only,
+ * the results do not depend on it. */
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
 
 #define ORC_MAXDIM 4
 

@@ -240,8 +240,9 @@ MCLAHE_API mclahe_status mclahe_backward(mclahe_plan_t plan, const float *d_in, 
  * different shapes, dimensionalities and parameters (no counterpart in the
  * paper).  Each phase runs as one persistent launch over a work list that
  * spans all volumes.  With use_graph != 0 the launches are captured once into
- * a CUDA graph cached in plans[0] and replayed on later calls with the same
- * pointers.
+ * a CUDA graph, cached by the library per (plans, pointers) for the process,
+ * and replayed on later calls with the same plans and pointers; destroying
+ * any of the plans drops the graphs that use it.
  *   plans     n_vol plans.
  *   d_in      host array of n_vol device input pointers.
  *   d_out     host array of n_vol device output pointers.

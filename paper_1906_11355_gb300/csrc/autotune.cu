@@ -81,6 +81,7 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
             p->t = it->second;
             p->t.bwd_chunks = bwd;
             p->tuned = 1;
+            batch_forget_plan(p);
             return MCLAHE_OK;
         }
     }
@@ -178,6 +179,7 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
     }
     p->t = best;
     p->tuned = 1;
+    batch_forget_plan(p);   // batched graphs captured with the old shapes
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tuned[key] = best;
     return MCLAHE_OK;

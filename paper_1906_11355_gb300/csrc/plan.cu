@@ -333,6 +333,7 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     p->t.hist_walk = hist_walk;
     p->t.hist_threads = hist_threads;
     p->tuned = 2;
+    batch_forget_plan(p);   // batched graphs captured with the old shapes
     return MCLAHE_OK;
 }
 

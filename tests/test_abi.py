@@ -63,6 +63,8 @@ def test_plan_geometry_matches_oracle(nat, orc, shape, ks):
 
 @pytest.mark.parametrize("kw", [
     dict(shape=(8, 8), ks=(9, 2)),            # kernel larger than the volume
+    dict(shape=(0, 8), ks=(1, 2)),            # empty volume
+    dict(shape=(8, 0), ks=(2, 1)),
     dict(shape=(8, 8), ks=(0, 2)),
     dict(shape=(8, 8), ks=(2,)),              # rank mismatch
     dict(shape=(8, 8, 8, 8, 8), ks=(2,) * 5),  # five dims

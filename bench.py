@@ -58,6 +58,8 @@ def parse():
                     help="keep the plan's default launch shapes (mclahe_autotune is skipped)")
     ap.add_argument("--shapes", default=None,
                     help="launch shapes as JSON (the keys of MCLAHE.set_shapes) instead of autotuning")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time mclahe_forward instead of the graph-replayed mclahe_forward_graph")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and forward+backward forms")
@@ -454,10 +456,13 @@ def run_native(args):
     passes = list(range(nat.MCLAHE_N_PASSES))
     launches = {p: nat.mclahe_pass_launches(op.plan, p) for p in passes}
 
-    # a step: one mclahe_forward (all passes) between two events
+    # a step: one forward call (all passes; by default replayed from the CUDA
+    # graph mclahe_forward_graph caches) between two events
+    fwd = nat.mclahe_forward if args.no_graph else nat.mclahe_forward_graph
+
     def step(e0, e1):
         e0.record(stream)
-        nat.mclahe_forward(op.plan, x, out, op.ws, op.ws_bytes, None, stream)
+        fwd(op.plan, x, out, op.ws, op.ws_bytes, None, stream)
         e1.record(stream)
 
     # the per-pass breakdown: each pass between events (an extra loop, untimed
@@ -571,6 +576,7 @@ def run_native(args):
                    "range": "adaptive" if w["adaptive"] else "global",
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "launch_shapes": shapes,
+                   "call": "mclahe_forward" if args.no_graph else "mclahe_forward_graph",
                    "voxels_per_gpu": voxels},
         "hbm_roofline_frac_whole_step": whole / peak,
         "ms_per_step_median": ms_median,

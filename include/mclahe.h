@@ -179,6 +179,20 @@ MCLAHE_API size_t mclahe_workspace_bytes(mclahe_plan_t plan);
 MCLAHE_API mclahe_status mclahe_forward(mclahe_plan_t plan, const float *d_in, float *d_out, void *d_ws,
                              size_t ws_bytes, const float *d_clip, mclahe_stream_t stream);
 
+/*
+ * mclahe_forward_graph -- mclahe_forward through a CUDA graph: the forward's
+ * launches (the clear, range, histogram and mapping passes) are captured once
+ * per (plan, d_in, d_out, d_ws, d_clip) and device into a graph the library
+ * caches for the process, and replayed on `stream` by every call with the
+ * same arguments (no counterpart in the paper).  For small volumes, whose
+ * passes are a few microseconds each, this removes the per-launch costs.
+ * Arguments and errors as for mclahe_forward; changing the plan's launch
+ * shapes or destroying it drops its graphs.
+ */
+MCLAHE_API mclahe_status mclahe_forward_graph(mclahe_plan_t plan, const float *d_in, float *d_out,
+                                              void *d_ws, size_t ws_bytes, const float *d_clip,
+                                              mclahe_stream_t stream);
+
 /* The passes of mclahe_forward, in the order it runs them. */
 typedef enum {
     MCLAHE_PASS_CLEAR = 0,  /* zero what later passes accumulate with atomics (memset): the

@@ -33,7 +33,7 @@ EXPORTS = (
     "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
-    "mclahe_plan_set_shapes",
+    "mclahe_plan_set_shapes", "mclahe_forward_graph",
 )
 
 MCLAHE_NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         lib.mclahe_workspace_bytes.restype = sz
         lib.mclahe_forward.argtypes = [vp, vp, vp, vp, sz, vp, vp]
         lib.mclahe_forward.restype = ctypes.c_int
+        lib.mclahe_forward_graph.argtypes = [vp, vp, vp, vp, sz, vp, vp]
+        lib.mclahe_forward_graph.restype = ctypes.c_int
         lib.mclahe_backward.argtypes = [vp, vp, vp, vp, sz, vp, vp, vp, vp]
         lib.mclahe_backward.restype = ctypes.c_int
         lib.mclahe_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -224,6 +226,12 @@ def mclahe_forward(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
     st = load().mclahe_forward(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
                                _ptr(d_clip), _stream(stream))
     _check(st, "mclahe_forward")
+
+
+def mclahe_forward_graph(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
+    st = load().mclahe_forward_graph(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
+                                     _ptr(d_clip), _stream(stream))
+    _check(st, "mclahe_forward_graph")
 
 
 def mclahe_forward_noalloc(plan, d_in, d_out, d_clip=None, stream=None):

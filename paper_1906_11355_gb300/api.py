@@ -45,14 +45,16 @@ class MCLAHE:
         if tuple(x.shape) != self.shape:
             raise ValueError(f"expected shape {self.shape}, got {tuple(x.shape)}")
 
-    def forward(self, x, out=None, clip=None, stream=None):
+    def forward(self, x, out=None, clip=None, stream=None, graph=False):
         """Run Algorithm 1 on x; returns out (allocated if not given).
 
-        clip: optional 1-element float32 CUDA tensor overriding the clip limit."""
+        clip: optional 1-element float32 CUDA tensor overriding the clip limit.
+        graph: replay a CUDA graph cached per (x, out, clip) (mclahe_forward_graph)."""
         self._check_volume(x)
         if out is None:
             out = torch.empty_like(x)
-        nat.mclahe_forward(self.plan, x, out, self.ws, self.ws_bytes, clip, stream)
+        fwd = nat.mclahe_forward_graph if graph else nat.mclahe_forward
+        fwd(self.plan, x, out, self.ws, self.ws_bytes, clip, stream)
         return out
 
     __call__ = forward

@@ -200,6 +200,44 @@ struct GraphKey {
 std::mutex g_graph_mutex;
 std::map<GraphKey, cudaGraphExec_t> g_graphs;
 
+// Replay the graph cached under key (plus the current device) on st; on the
+// first call capture enqueue(capture stream) into it.
+template <typename Enqueue>
+mclahe_status replay_cached(GraphKey key, cudaStream_t st, Enqueue &&enqueue) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    key.ptrs.push_back(reinterpret_cast<const void *>(intptr_t(dev)));
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_graph_mutex);
+        auto it = g_graphs.find(key);
+        if (it != g_graphs.end()) exec = it->second;
+    }
+    if (!exec) {
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return MCLAHE_ERR_CUDA;
+        cudaGraph_t graph = nullptr;
+        mclahe_status s = MCLAHE_OK;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            s = MCLAHE_ERR_CUDA;
+        } else {
+            s = enqueue(cap);
+            if (cudaStreamEndCapture(cap, &graph) != cudaSuccess && s == MCLAHE_OK) s = MCLAHE_ERR_CUDA;
+        }
+        if (s == MCLAHE_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) s = MCLAHE_ERR_CUDA;
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (s != MCLAHE_OK) return s;
+        std::lock_guard<std::mutex> lock(g_graph_mutex);
+        auto ins = g_graphs.emplace(key, exec);
+        if (!ins.second) {   // another thread cached the same graph meanwhile
+            cudaGraphExecDestroy(exec);
+            exec = ins.first->second;
+        }
+    }
+    return cudaGraphLaunch(exec, st) == cudaSuccess ? MCLAHE_OK : MCLAHE_ERR_CUDA;
+}
+
 }  // namespace
 
 void batch_forget_plan(const mclahe_plan_s *p) {
@@ -252,38 +290,22 @@ mclahe_status mclahe_batch(int n_vol, const mclahe_plan_t *plans, const float *c
     }
     key.ptrs.push_back(d_ws);
     key.ptrs.push_back(d_clip);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    key.ptrs.push_back(reinterpret_cast<const void *>(intptr_t(dev)));
-    cudaGraphExec_t exec = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_graph_mutex);
-        auto it = g_graphs.find(key);
-        if (it != g_graphs.end()) exec = it->second;
-    }
-    if (!exec) {
-        cudaStream_t cap;
-        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return MCLAHE_ERR_CUDA;
-        cudaGraph_t graph = nullptr;
-        mclahe_status s = MCLAHE_OK;
-        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            s = MCLAHE_ERR_CUDA;
-        } else {
-            s = enqueue_batch(n_vol, plans, d_in, d_out, ws, d_clip, cap);
-            if (cudaStreamEndCapture(cap, &graph) != cudaSuccess && s == MCLAHE_OK) s = MCLAHE_ERR_CUDA;
-        }
-        if (s == MCLAHE_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) s = MCLAHE_ERR_CUDA;
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cap);
-        if (s != MCLAHE_OK) return s;
-        std::lock_guard<std::mutex> lock(g_graph_mutex);
-        auto ins = g_graphs.emplace(key, exec);
-        if (!ins.second) {   // another thread cached the same batch meanwhile
-            cudaGraphExecDestroy(exec);
-            exec = ins.first->second;
-        }
-    }
-    return cudaGraphLaunch(exec, st) == cudaSuccess ? MCLAHE_OK : MCLAHE_ERR_CUDA;
+    return replay_cached(key, st, [&](cudaStream_t cap) {
+        return enqueue_batch(n_vol, plans, d_in, d_out, ws, d_clip, cap);
+    });
+}
+
+mclahe_status mclahe_forward_graph(mclahe_plan_t p, const float *d_in, float *d_out, void *d_ws,
+                                   size_t ws_bytes, const float *d_clip, mclahe_stream_t stream) {
+    mclahe_status s = check_forward_args(p, d_in, d_out, d_ws, ws_bytes);
+    if (s != MCLAHE_OK) return s;
+    GraphKey key;
+    // the forward's key carries a tag that no batch key has in that slot
+    key.ptrs = {reinterpret_cast<const void *>(uintptr_t(1)), p, d_in, d_out, d_ws, d_clip};
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    return replay_cached(key, reinterpret_cast<cudaStream_t>(stream), [&](cudaStream_t cap) {
+        return forward_impl(*p, d_in, d_out, ws, d_clip, cap);
+    });
 }
 
 }  // extern "C"

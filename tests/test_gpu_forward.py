@@ -198,6 +198,35 @@ def test_tma_mapping_rejected_where_rows_are_unaligned(torch_cuda):
         op.set_shapes(**sh)
 
 
+@pytest.mark.parametrize("case", [((512, 512), (64, 64), 256, 0.01, False),
+                                  ((16, 64, 64), (4, 16, 16), 256, 0.02, True),
+                                  ((6, 10, 12, 16), (3, 5, 4, 8), 512, 0.01, False)],
+                         ids=["2dG", "3dA", "4dG"])
+def test_graph_forward_equals_forward(torch_cuda, orc, case):
+    """mclahe_forward_graph replays the same launches: bit-equal to mclahe_forward, on
+    repeated calls and new contents of the same buffers, and after a shape change."""
+    torch = torch_cuda
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    shape, ks, nb, clip, adaptive = case
+    rng = np.random.default_rng(5)
+    op = MCLAHE(shape, ks, nb, f32(clip), adaptive)
+    x = torch.empty(shape, device="cuda")
+    a, b = torch.empty_like(x), torch.empty_like(x)
+    for rep in range(3):
+        x.copy_(torch.from_numpy(rng.gamma(2.0, 1.0, size=shape).astype(np.float32)))
+        op.forward(x, out=a)
+        op.forward(x, out=b, graph=True)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), rep
+        if rep == 1:   # new launch shapes: the cached graph is dropped and recaptured
+            sh = op.shapes()
+            sh["map_chunks"] = 2 if sh["map_chunks"] == 1 else 1
+            op.set_shapes(**sh)
+    want = orc.mclahe(x.cpu().numpy(), ks, nb, f32(clip), mode=int(adaptive))
+    assert np.abs(b.cpu().numpy().astype(np.float64) - want).max() <= OUT_TOL
+
+
 def test_given_global_range_and_out_of_range_values(torch_cuda, orc):
     rng = np.random.default_rng(5)
     x = rng.normal(0.5, 0.4, size=(40, 50)).astype(np.float32)

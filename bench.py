@@ -41,8 +41,8 @@ def pass_kernel(pass_name, info):
     flat = info["hist_shares"] > 0
     if pass_name == "range":
         return "k_hist_flat" if (flat and info["mode"] == 1) else "k_range_global"
-    return {"hist": "k_hist_flat" if flat else "k_hist",
-            "map": "k_map_tma" if info["map_tma"] else "k_map"}[pass_name]
+    mapk = "k_map_tma" if info["map_tma"] else ("k_map_flat" if info["map_flat"] else "k_map")
+    return {"hist": "k_hist_flat" if flat else "k_hist", "map": mapk}[pass_name]
 
 
 
@@ -449,7 +449,7 @@ def run_native(args):
     elif not args.no_autotune:
         op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
     shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
-              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk", "hist_threads",
+              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk", "hist_threads", "map_flat",
                        "map_chunks", "map_tma", "tuned")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -127,7 +127,8 @@ typedef struct {
     int32_t hist_walk;            /* rows of the histogram pass: 0 cp.async ring, 1 TMA box
                                      tiles, 2 per-thread loads (least shared memory) */
     int32_t hist_threads;         /* threads per histogram CTA (256; 512 allowed for 4-D) */
-    int32_t reserved;
+    int32_t map_flat;             /* 1: the mapping pass deals map_chunks shares per cell out to
+                                     a persistent grid (per-thread walk only) */
 } mclahe_plan_info;
 
 /*
@@ -296,6 +297,8 @@ MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, 
  *   map_chunks    CTAs per inter-kernel cell in the mapping pass, 1..64.
  *   map_tma       0: per-thread loads and stores; 1: TMA box tiles (3- and 4-D volumes
  *                 whose last dim and cell rows start on 16-byte boundaries only).
+ *   map_flat      0: one CTA per chunk of a cell; 1: map_chunks row shares per cell dealt
+ *                 out in order to a persistent grid (map_tma = 0 only).
  * Returns MCLAHE_ERR_INVALID_ARG (plan unchanged) for values outside these
  * ranges, a histogram CTA above 220 KiB of shared memory, or hist_walk = 1 or
  * map_tma = 1 on a geometry that does not allow it.  Sets tuned = 2.
@@ -304,7 +307,7 @@ MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist
                                                 int32_t hist_cluster, int32_t hist_copies,
                                                 int32_t hist_shares, int32_t hist_walk,
                                                 int32_t hist_threads, int32_t map_chunks,
-                                                int32_t map_tma);
+                                                int32_t map_tma, int32_t map_flat);
 
 /* Size of the library's built-in scratch array used by mclahe_forward_noalloc. */
 #define MCLAHE_NOALLOC_SCRATCH_BYTES (8u << 20)

@@ -60,7 +60,7 @@ class PlanInfo(ctypes.Structure):
         ("bwd_chunks", ctypes.c_int32), ("tuned", ctypes.c_int32),
         ("hist_shares", ctypes.c_int32), ("hist_ctas", ctypes.c_int32),
         ("map_tma", ctypes.c_int32), ("hist_walk", ctypes.c_int32),
-        ("hist_threads", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("hist_threads", ctypes.c_int32), ("map_flat", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -126,7 +126,7 @@ def load(path: str = LIB_PATH):
         lib.mclahe_pass_launches.restype = ctypes.c_int
         lib.mclahe_forward_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.mclahe_forward_noalloc.restype = ctypes.c_int
-        lib.mclahe_plan_set_shapes.argtypes = [vp] + [ctypes.c_int32] * 8
+        lib.mclahe_plan_set_shapes.argtypes = [vp] + [ctypes.c_int32] * 9
         lib.mclahe_plan_set_shapes.restype = ctypes.c_int
         lib.mclahe_version.argtypes = []
         lib.mclahe_version.restype = ctypes.c_int
@@ -211,10 +211,11 @@ def mclahe_plan_query(plan) -> dict:
 
 
 def mclahe_plan_set_shapes(plan, hist_group, hist_cluster, hist_copies, hist_shares, map_chunks,
-                           map_tma=0, hist_walk=0, hist_threads=256):
+                           map_tma=0, hist_walk=0, hist_threads=256, map_flat=0):
     _check(load().mclahe_plan_set_shapes(plan.handle, int(hist_group), int(hist_cluster),
                                          int(hist_copies), int(hist_shares), int(hist_walk),
-                                         int(hist_threads), int(map_chunks), int(map_tma)),
+                                         int(hist_threads), int(map_chunks), int(map_tma),
+                                         int(map_flat)),
            "mclahe_plan_set_shapes")
 
 

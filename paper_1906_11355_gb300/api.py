@@ -71,13 +71,13 @@ class MCLAHE:
         info = nat.mclahe_plan_query(self.plan)
         return {k: int(info[k]) for k in ("hist_group", "hist_cluster", "hist_copies",
                                           "hist_shares", "hist_walk", "hist_threads", "map_chunks",
-                                          "map_tma")}
+                                          "map_tma", "map_flat")}
 
     def set_shapes(self, hist_group, hist_cluster, hist_copies, hist_shares, map_chunks,
-                   map_tma=0, hist_walk=0, hist_threads=256):
+                   map_tma=0, hist_walk=0, hist_threads=256, map_flat=0):
         """Set launch shapes explicitly (e.g. from another process's autotune)."""
         nat.mclahe_plan_set_shapes(self.plan, hist_group, hist_cluster, hist_copies, hist_shares,
-                                   map_chunks, map_tma, hist_walk, hist_threads)
+                                   map_chunks, map_tma, hist_walk, hist_threads, map_flat)
 
     # views into the workspace left by the last forward call
     def _view(self, key, count, dtype):

@@ -155,8 +155,10 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
         best_ms = 1e30f;
         int bx, by, bz;
         const int n_walks = map_tma_box(p->g, bx, by, bz) ? 2 : 1;
-        for (int tma = 0; tma < n_walks; ++tma) {
-            p->t.map_tma = tma;
+        // walks: per-thread (per-cell grid), per-thread (flat grid), TMA tiles
+        for (int walk = 0; walk < 2 + (n_walks > 1 ? 1 : 0); ++walk) {
+            p->t.map_tma = walk == 2 ? 1 : 0;
+            p->t.map_flat = walk == 1 ? 1 : 0;
             for (int mc = 1; mc <= 64 && mc <= rows && s == MCLAHE_OK; mc <<= 1) {
                 p->t.map_chunks = mc;
                 const float ms =
@@ -164,7 +166,8 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
                 if (ms >= 0.0f && ms < best_ms) {
                     best_ms = ms;
                     best.map_chunks = mc;
-                    best.map_tma = tma;
+                    best.map_tma = p->t.map_tma;
+                    best.map_flat = p->t.map_flat;
                 }
             }
         }

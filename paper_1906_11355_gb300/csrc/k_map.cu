@@ -37,6 +37,29 @@ __global__ void __launch_bounds__(kTmaConsumers + 32, D >= 4 ? (ADAPTIVE ? 1 : 2
     map_cell<D, ADAPTIVE, true, kWalkTma>(g, in, out, lut, lo_k, scale_k, cell, chunk, chunks, tab, &t);
 }
 
+// Flat form: every cell is cut into `shares` equal row shares, and the shares
+// of all cells are dealt out in order to a persistent grid (one wave), so the
+// CTAs' work is equal whatever the number of cells; a CTA restages the corner
+// tables when its range moves to the next cell.
+template <int D, bool ADAPTIVE, bool REPL>
+__global__ void __launch_bounds__(256, D >= 4 ? (ADAPTIVE ? 1 : 2) : (ADAPTIVE && D == 3 ? 2 : 3))
+    k_map_flat(Geom g, const float *__restrict__ in, float *__restrict__ out,
+               const float *__restrict__ lut, const float *__restrict__ lo_k,
+               const float *__restrict__ scale_k, int shares, int64_t total) {
+    extern __shared__ __align__(16) float tab[];
+    const int64_t b0 = total * blockIdx.x / gridDim.x;
+    const int64_t b1 = total * (blockIdx.x + 1) / gridDim.x;
+    for (int64_t s = b0; s < b1;) {
+        const int64_t cell = s / shares;
+        const int c0 = int(s - cell * shares);
+        const int64_t rest = b1 - cell * shares;
+        const int c1 = rest < shares ? int(rest) : shares;
+        map_cell<D, ADAPTIVE, REPL>(g, in, out, lut, lo_k, scale_k, cell, c0, shares, tab, nullptr, c1);
+        s = cell * shares + c1;
+        __syncthreads();   // the tables are restaged for the next cell
+    }
+}
+
 bool map_replicated(const Geom &g) { return map_repl_fits(g.P); }
 size_t map_smem_bytes(const Geom &g) { return map_smem_for(g.D, g.P); }
 
@@ -86,9 +109,29 @@ static cudaError_t launch_map_tma_t(const mclahe_plan_s &p, const float *in, flo
 }
 
 template <int D, bool A, bool REPL>
+static cudaError_t launch_map_flat_t(const mclahe_plan_s &p, const float *in, float *out,
+                                     const unsigned char *ws, cudaStream_t st, size_t smem) {
+    auto kern = k_map_flat<D, A, REPL>;
+    cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cached_occupancy(reinterpret_cast<const void *>(kern), p.t.map_threads, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t total = n_cells(p.g) * p.t.map_chunks;
+    const unsigned grid = unsigned(std::min<int64_t>(total, int64_t(per_sm) * device_sms()));
+    kern<<<grid, p.t.map_threads, smem, st>>>(
+        p.g, in, out, reinterpret_cast<const float *>(ws + p.ws.lut),
+        reinterpret_cast<const float *>(ws + p.ws.lo), reinterpret_cast<const float *>(ws + p.ws.scale),
+        p.t.map_chunks, total);
+    return cudaGetLastError();
+}
+
+template <int D, bool A, bool REPL>
 static cudaError_t launch_map_t(const mclahe_plan_s &p, const float *in, float *out,
                                 const unsigned char *ws, cudaStream_t st, unsigned grid,
                                 size_t smem) {
+    if (p.t.map_flat) return launch_map_flat_t<D, A, REPL>(p, in, out, ws, st, smem);
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_map<D, A, REPL>), smem);
     if (e != cudaSuccess) return e;
     k_map<D, A, REPL><<<grid, p.t.map_threads, smem, st>>>(

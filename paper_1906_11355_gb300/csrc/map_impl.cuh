@@ -104,7 +104,11 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                                          float *__restrict__ out, const float *__restrict__ lut,
                                          const float *__restrict__ lo_k,
                                          const float *__restrict__ scale_k, int64_t cell, int chunk,
-                                         int chunks, float *tab, const MapTma *tma = nullptr) {
+                                         int chunks, float *tab, const MapTma *tma = nullptr,
+                                         int chunk_end = -1) {
+    // rows [R * chunk / chunks, R * chunk_end / chunks) of the cell (chunk_end
+    // defaults to chunk + 1)
+    if (chunk_end < 0) chunk_end = chunk + 1;
     constexpr bool RING = WALK == kWalkRing;
     constexpr int NC = 1 << D;          // corners
     constexpr int NO = 1 << (D - 1);    // corners over dims 0..D-2
@@ -195,7 +199,7 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
 #pragma unroll
     for (int j = 0; j < D - 1; ++j) R *= len[j];
     const int r0 = int((int64_t(R) * chunk) / chunks);
-    const int r1 = int((int64_t(R) * (chunk + 1)) / chunks);
+    const int r1 = int((int64_t(R) * chunk_end) / chunks);
     __syncthreads();
 
     // per-dim weight constants: w1 = float(2 x + mb_j) * inv2b_j

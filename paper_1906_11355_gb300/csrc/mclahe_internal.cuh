@@ -81,6 +81,7 @@ struct Tuning {
     int map_threads;    // threads per mapping CTA
     int map_chunks;     // CTAs per inter-kernel cell in the mapping pass
     int map_tma;        // 1: stream 3- and 4-D cells as TMA tiles (where map_tma_box allows)
+    int map_flat;       // 1: map_chunks shares per cell dealt out to a persistent grid
     int hist_walk;      // rows of the histogram pass: 0 cp.async ring, 1 TMA tiles (where
                         // hist_tma_box allows), 2 per-thread loads (least shared memory)
     int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)

@@ -85,6 +85,7 @@ Tuning default_tuning(const Geom &g) {
     // requests would touch a line per 32 bytes
     int bx, by, bz;
     t.map_tma = (map_tma_box(g, bx, by, bz) && dl.b < 32) ? 1 : 0;
+    t.map_flat = 0;
     t.hist_walk = 0;
     int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
     bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
@@ -299,6 +300,7 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->map_tma = p->t.map_tma;
     info->hist_walk = p->t.hist_walk;
     info->hist_threads = p->t.hist_threads;
+    info->map_flat = p->t.map_flat;
     info->hist_copies = p->t.hist_copies;
     info->map_chunks = p->t.map_chunks;
     info->bwd_chunks = p->t.bwd_chunks;
@@ -308,7 +310,8 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
 
 mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_t hist_cluster,
                                      int32_t hist_copies, int32_t hist_shares, int32_t hist_walk,
-                                     int32_t hist_threads, int32_t map_chunks, int32_t map_tma) {
+                                     int32_t hist_threads, int32_t map_chunks, int32_t map_tma,
+                                     int32_t map_flat) {
     if (!p) return MCLAHE_ERR_INVALID_ARG;
     auto pow2 = [](int32_t v, int32_t hi) { return v >= 1 && v <= hi && (v & (v - 1)) == 0; };
     const Geom &g = p->g;
@@ -319,6 +322,7 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     if (map_chunks < 1 || map_chunks > 64) return MCLAHE_ERR_INVALID_ARG;
     int bx, by, bz;
     if (map_tma != 0 && (map_tma != 1 || !map_tma_box(g, bx, by, bz))) return MCLAHE_ERR_INVALID_ARG;
+    if (map_flat != 0 && (map_flat != 1 || map_tma != 0)) return MCLAHE_ERR_INVALID_ARG;
     if (hist_walk < 0 || hist_walk > 2 || (hist_walk == 1 && !hist_tma_box(g, hist_group, bx, by)))
         return MCLAHE_ERR_INVALID_ARG;
     if (hist_threads != 256 && !(hist_threads == 512 && g.D >= 4)) return MCLAHE_ERR_INVALID_ARG;
@@ -330,6 +334,7 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     p->t.hist_shares = hist_shares;
     p->t.map_chunks = map_chunks;
     p->t.map_tma = map_tma;
+    p->t.map_flat = map_flat;
     p->t.hist_walk = hist_walk;
     p->t.hist_threads = hist_threads;
     p->tuned = 2;

@@ -96,7 +96,9 @@ FORMS = [dict(hist_group=1, hist_cluster=4, hist_copies=4, hist_shares=0, map_ch
               hist_threads=512),
          dict(hist_group=1, hist_cluster=1, hist_copies=8, hist_shares=1, map_chunks=1),
          dict(hist_group=2, hist_cluster=1, hist_copies=2, hist_shares=7, map_chunks=1),
-         dict(hist_group=1, hist_cluster=1, hist_copies=16, hist_shares=300, map_chunks=3)]
+         dict(hist_group=1, hist_cluster=1, hist_copies=16, hist_shares=300, map_chunks=3),
+         dict(hist_group=1, hist_cluster=2, hist_copies=8, hist_shares=0, map_chunks=5,
+              map_flat=1)]
 
 
 @pytest.mark.parametrize("form", range(len(FORMS)))

@@ -222,15 +222,24 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
     constexpr int NA = ADAPTIVE ? NC : 1;
     float2 anlo[ADAPTIVE ? NC / 2 : 1], asc[ADAPTIVE ? NC / 2 : 1];
     uint32_t cbase[NA];
+    // AHR: the 1/qk of the quantiser folded into the corners' scales when
+    // that is exact for all of them (the same decision in every thread)
+    bool fold = false;
     if (ADAPTIVE) {
         float nl[NA], sc[NA];
+        fold = true;
 #pragma unroll
         for (int t = 0; t < NA; ++t) {
             const int c = REPL ? ((t + rot) & (NC - 1)) : t;
             nl[t] = s_nlo[c];
             sc[t] = s_sc[c];
+            fold = fold && fold_exact(sc[t], g.iqk);
             const int slot = REPL ? ((lane & ~(NC - 1) & 31) | c) : c;
             cbase[t] = tab_s + 4u * uint32_t(slot) - kBinBias * RSB;
+        }
+        if (fold) {
+#pragma unroll
+            for (int t = 0; t < NA; ++t) sc[t] *= g.iqk;
         }
 #pragma unroll
         for (int t = 0; t < NA / 2; ++t) {
@@ -324,11 +333,43 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
 
     const int rodd = rot & 1;
     const float two_inv2b = 2.0f * inv2b_l;
+    // AHR: the step sums (acc.x, acc.y) hold last-dim sides (rodd, 1 - rodd),
+    // whose weights at last-dim weight w1 are wab.x * w1 + wab.y and
+    // -wab.x * w1 + (1 - wab.y); dwe is their change from one voxel to the next
+    const float2 wab = rodd ? make_float2(1.0f, 0.0f) : make_float2(-1.0f, 1.0f);
+    const float2 dwe = make_float2(wab.x * two_inv2b, -wab.x * two_inv2b);
+    // AHR quad: quantise per corner pair, gather, and weight the two sides
+    auto map4a = [&](const MRow &st, const float (&vals)[4], float fbi, float (&res)[4], auto folded) {
+        constexpr bool FOLD = decltype(folded)::value;
+        const float2 w0 = __ffma2_rn(make_float2(fbi, fbi), make_float2(wab.x, -wab.x),
+                                     make_float2(wab.y, 1.0f - wab.y));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float2 acc = make_float2(0.0f, 0.0f);
+            const float2 xx = make_float2(vals[e], vals[e]);
+#pragma unroll
+            for (int t = 0; t < NA / 2; ++t) {
+                const uint2 b = FOLD ? qbits2_folded(xx, anlo[t], asc[t], qkf)
+                                     : qbits2(xx, anlo[t], asc[t], iqk, qkf);
+                const float v0 = lds_f32(b.x * RSB + cbase[2 * t]);
+                const float v1 = lds_f32(b.y * RSB + cbase[2 * t + 1]);
+                acc = __ffma2_rn(make_float2(v0, v1), st.w[t], acc);
+            }
+            const float2 we = e == 0 ? w0 : __ffma2_rn(make_float2(float(e), float(e)), dwe, w0);
+            res[e] = fmaf(acc.y, we.y, acc.x * we.x);
+        }
+    };
     // the mapping of the four voxels of a quad (vals) at last-dim weight
     // w1 = fbi + e * two_inv2b for voxel e
     auto map4 = [&](const MRow &st, const float (&vals)[4], float fbi, float (&res)[4]) {
-        uint32_t gb[4];
-        if (!ADAPTIVE) {
+        if constexpr (ADAPTIVE) {
+            if (fold)
+                map4a(st, vals, fbi, res, std::true_type{});
+            else
+                map4a(st, vals, fbi, res, std::false_type{});
+        } else {
+            // GHR: one bin per voxel for all corners
+            uint32_t gb[4];
             const float2 nl = make_float2(gnlo, gnlo), sc = make_float2(gsc, gsc);
             const uint2 b01 = qbits2(make_float2(vals[0], vals[1]), nl, sc, iqk, qkf);
             const uint2 b23 = qbits2(make_float2(vals[2], vals[3]), nl, sc, iqk, qkf);
@@ -336,44 +377,31 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             gb[1] = b01.y;
             gb[2] = b23.x;
             gb[3] = b23.y;
-        }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float w1 = fmaf(float(e), two_inv2b, fbi);
-            float a0, a1;   // sums over the outer corners at last-dim side 0 and 1
-            if (ADAPTIVE) {
-                float2 acc = make_float2(0.0f, 0.0f);
-                const float2 xx = make_float2(vals[e], vals[e]);
+            for (int e = 0; e < 4; ++e) {
+                const float w1 = fmaf(float(e), two_inv2b, fbi);
+                float a0, a1;   // sums over the outer corners at last-dim side 0 and 1
+                if (gb[e] == kBinBias) {
+                    // bin 0: every table's first entry is 0, so the voxel maps to 0
+                    a0 = 0.0f;
+                    a1 = 0.0f;
+                } else if (NC >= 4) {
+                    float2 acc0 = make_float2(0.0f, 0.0f), acc1 = acc0;   // sides 0 and 1
 #pragma unroll
-                for (int t = 0; t < NA / 2; ++t) {
-                    const uint2 b = qbits2(xx, anlo[t], asc[t], iqk, qkf);
-                    const float v0 = lds_f32(b.x * RSB + cbase[2 * t]);
-                    const float v1 = lds_f32(b.y * RSB + cbase[2 * t + 1]);
-                    acc = __ffma2_rn(make_float2(v0, v1), st.w[t], acc);
+                    for (int s = 0; s < NQ; ++s) {
+                        const float4 t4 = lds_f32x4(gb[e] * RSB + gbase[s]);
+                        acc0 = __ffma2_rn(make_float2(t4.x, t4.y), st.w[s], acc0);
+                        acc1 = __ffma2_rn(make_float2(t4.z, t4.w), st.w[s], acc1);
+                    }
+                    a0 = acc0.x + acc0.y;
+                    a1 = acc1.x + acc1.y;
+                } else {
+                    const float2 t2 = lds_f32x2(gb[e] * RSB + gbase[0]);
+                    a0 = t2.x;
+                    a1 = t2.y;
                 }
-                // even steps read last-dim side rot & 1, odd steps the other
-                a0 = rodd ? acc.y : acc.x;
-                a1 = rodd ? acc.x : acc.y;
-            } else if (gb[e] == kBinBias) {
-                // bin 0: every table's first entry is 0, so the voxel maps to 0
-                a0 = 0.0f;
-                a1 = 0.0f;
-            } else if (NC >= 4) {
-                float2 acc0 = make_float2(0.0f, 0.0f), acc1 = acc0;   // sides 0 and 1
-#pragma unroll
-                for (int s = 0; s < NQ; ++s) {
-                    const float4 t4 = lds_f32x4(gb[e] * RSB + gbase[s]);
-                    acc0 = __ffma2_rn(make_float2(t4.x, t4.y), st.w[s], acc0);
-                    acc1 = __ffma2_rn(make_float2(t4.z, t4.w), st.w[s], acc1);
-                }
-                a0 = acc0.x + acc0.y;
-                a1 = acc1.x + acc1.y;
-            } else {
-                const float2 t2 = lds_f32x2(gb[e] * RSB + gbase[0]);
-                a0 = t2.x;
-                a1 = t2.y;
+                res[e] = fmaf(w1, a1 - a0, a0);
             }
-            res[e] = fmaf(w1, a1 - a0, a0);
         }
     };
     auto store4 = [&](int64_t a, int e0, const float (&res)[4]) {

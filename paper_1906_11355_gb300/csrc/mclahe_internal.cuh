@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -168,6 +169,23 @@ __device__ __forceinline__ uint2 qbits2(float2 x, float2 nlo, float2 sc, float i
     y.y = mul_sat(y.y, iqk);
     y = __ffma2_rd(y, make_float2(qkf, qkf), make_float2(kTwo23, kTwo23));
     return make_uint2(__float_as_uint(y.x), __float_as_uint(y.y));
+}
+
+// qbits2 with the 2^-k of iqk folded into the scale (scq = sc * iqk).  Equal
+// to qbits2 whenever scq is exact, that is, sc is zero, infinite, NaN or
+// scq is a normal number (fold_exact): 1/qk is a power of two, so rounding
+// (x - lo) * scq equals rounding (x - lo) * sc and then scaling by 1/qk in
+// the normal range, and a product below the normal range is bin 0 either way.
+__device__ __forceinline__ uint2 qbits2_folded(float2 x, float2 nlo, float2 scq, float qkf) {
+    float2 y = __fadd2_rn(x, nlo);
+    y.x = mul_sat(y.x, scq.x);
+    y.y = mul_sat(y.y, scq.y);
+    y = __ffma2_rd(y, make_float2(qkf, qkf), make_float2(kTwo23, kTwo23));
+    return make_uint2(__float_as_uint(y.x), __float_as_uint(y.y));
+}
+
+__device__ __forceinline__ bool fold_exact(float sc, float iqk) {
+    return sc == 0.0f || !(fabsf(sc * iqk) < 1.17549435e-38f);
 }
 
 __device__ __forceinline__ uint32_t qbits1(float x, float nlo, float sc, float iqk, float qkf) {

@@ -446,11 +446,29 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             int c[R];     // box origin, innermost first
             bool full;    // the box lies inside the cell (TMA store)
         };
-        auto tile = [&](int k) {
-            Tile t;
+        // position of a tile in the cell's order (slice, block along D-2,
+        // block along 1); every walker visits its tiles in order, so it steps
+        // this forward instead of dividing per tile
+        struct TilePos {
+            int sl, yb, zb;
+        };
+        auto tile_pos = [&](int k) {
             const int kk = kb + k;
-            const int sl = kk % n0, blk = kk / n0;
-            const int yb = blk % ny, zb = blk / ny;
+            const int blk = kk / n0;
+            return TilePos{kk - blk * n0, blk % ny, blk / ny};
+        };
+        auto step = [&](TilePos &q) {
+            if (++q.sl == n0) {
+                q.sl = 0;
+                if (++q.yb == ny) {
+                    q.yb = 0;
+                    ++q.zb;
+                }
+            }
+        };
+        auto tile = [&](const TilePos &q) {
+            Tile t;
+            const int sl = q.sl, yb = q.yb, zb = q.zb;
             t.c[0] = box_lo[D - 1];
             t.c[1] = box_lo[D - 2] + yb * By;
             if (D == 4) t.c[2] = box_lo[1] + zb * Bz;
@@ -475,8 +493,11 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         if (warp == NCW) {
             // ---- producer (one lane)
             if (lane == 0) {
+                TilePos lp = nt > 0 ? tile_pos(0) : TilePos{0, 0, 0};   // next load
+                TilePos rp = lp;                                         // next retire
                 auto load = [&](int k) {
-                    const Tile t = tile(k);
+                    const Tile t = tile(lp);
+                    step(lp);
                     const uint32_t st = uint32_t(k % NS);
                     mbar_expect_tx(full0 + 8u * st, tile_bytes);
                     tma_load<R>(stage0 + st * kStageBytes, tma->in, t.c, full0 + 8u * st);
@@ -487,7 +508,8 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
                     const uint32_t st = uint32_t(k % NS);
                     if (!mbar_wait_bounded(empty0 + 8u * st, uint32_t(k / NS) & 1u, kTmaWaitLimit))
                         gave_up();
-                    const Tile t = tile(k);
+                    const Tile t = tile(rp);
+                    step(rp);
                     if (t.full) {
                         tma_store<R>(tma->out, t.c, stage0 + st * kStageBytes);
                         bulk_commit();
@@ -525,16 +547,15 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         constexpr int NW = sizeof(MRow) / sizeof(float2);
         MRow inner[QT];
         uint32_t sel[QT];
-        int cur_blk = -1;
+        TilePos cq = nt > 0 ? tile_pos(0) : TilePos{0, 0, 0};
         for (int k = 0; k < nt; ++k) {
             const int stg = k % NS;
             if (!mbar_wait_bounded(full0 + 8u * uint32_t(stg), uint32_t(k / NS) & 1u, kTmaWaitLimit))
                 gave_up();
-            const Tile t = tile(k);
+            const Tile t = tile(cq);
             const uint32_t sbase = stage0 + uint32_t(stg) * kStageBytes;
-            const int blk = (kb + k) / n0;
-            if (blk != cur_blk) {
-                cur_blk = blk;
+            // a new block starts at the first tile and whenever the slice wraps
+            if (k == 0 || cq.sl == 0) {
 #pragma unroll
                 for (int i = 0; i < QT; ++i) {
                     int coords[kMaxDim];
@@ -600,6 +621,7 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             if (t.full) fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8u * uint32_t(stg));
+            step(cq);
         }
         return;
     }

@@ -152,6 +152,14 @@ def test_set_shapes_validates_and_round_trips(nat):
     assert nat.mclahe_plan_query(p4)["hist_threads"] == 512
     with pytest.raises(nat.MclaheError):
         nat.mclahe_plan_set_shapes(p4, 1, 1, 8, 0, 1, 0, hist_threads=384)
+    # flat mapping grid: 0 or 1, and not together with TMA tiles
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 8, 0, map_flat=1)
+    assert (nat.mclahe_plan_query(plan)["map_flat"], nat.mclahe_plan_query(plan)["map_chunks"]) == (1, 8)
+    for tma, flat in ((0, 2), (0, -1), (1, 1)):
+        with pytest.raises(nat.MclaheError):
+            nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 8, tma, map_flat=flat)
+    assert nat.mclahe_plan_query(plan)["map_flat"] == 1
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, map_flat=0)
     info = nat.mclahe_plan_query(plan)   # unchanged by the rejected calls
     assert (info["hist_group"], info["hist_cluster"], info["hist_copies"], info["hist_shares"],
-            info["map_chunks"]) == (1, 4, 16, 0, 1)
+            info["map_chunks"], info["map_flat"]) == (1, 4, 16, 0, 1, 0)

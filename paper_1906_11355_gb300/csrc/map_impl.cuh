@@ -233,7 +233,7 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
             const int c = REPL ? ((t + rot) & (NC - 1)) : t;
             nl[t] = s_nlo[c];
             sc[t] = s_sc[c];
-            fold = fold && fold_exact(sc[t], g.iqk);
+            fold = fold && fold_exact(sc[t], g.qkf);
             const int slot = REPL ? ((lane & ~(NC - 1) & 31) | c) : c;
             cbase[t] = tab_s + 4u * uint32_t(slot) - kBinBias * RSB;
         }

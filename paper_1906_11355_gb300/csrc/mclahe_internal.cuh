@@ -173,9 +173,12 @@ __device__ __forceinline__ uint2 qbits2(float2 x, float2 nlo, float2 sc, float i
 
 // qbits2 with the 2^-k of iqk folded into the scale (scq = sc * iqk).  Equal
 // to qbits2 whenever scq is exact, that is, sc is zero, infinite, NaN or
-// scq is a normal number (fold_exact): 1/qk is a power of two, so rounding
-// (x - lo) * scq equals rounding (x - lo) * sc and then scaling by 1/qk in
-// the normal range, and a product below the normal range is bin 0 either way.
+// |sc| >= 2^-126 * qk, so that sc * 2^-k is a normal number before rounding
+// (fold_exact; testing the rounded product instead would pass scales whose
+// product rounds up to the smallest normal): 1/qk is a power of two, so
+// rounding (x - lo) * scq equals rounding (x - lo) * sc and then scaling by
+// 1/qk in the normal range, and a product below the normal range is bin 0
+// either way.
 __device__ __forceinline__ uint2 qbits2_folded(float2 x, float2 nlo, float2 scq, float qkf) {
     float2 y = __fadd2_rn(x, nlo);
     y.x = mul_sat(y.x, scq.x);
@@ -184,8 +187,8 @@ __device__ __forceinline__ uint2 qbits2_folded(float2 x, float2 nlo, float2 scq,
     return make_uint2(__float_as_uint(y.x), __float_as_uint(y.y));
 }
 
-__device__ __forceinline__ bool fold_exact(float sc, float iqk) {
-    return sc == 0.0f || !(fabsf(sc * iqk) < 1.17549435e-38f);
+__device__ __forceinline__ bool fold_exact(float sc, float qkf) {
+    return sc == 0.0f || !(fabsf(sc) < 1.17549435e-38f * qkf);   // 2^-126 * qk, exact
 }
 
 __device__ __forceinline__ uint32_t qbits1(float x, float nlo, float sc, float iqk, float qkf) {

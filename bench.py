@@ -2,11 +2,14 @@
 """Throughput of the MCLAHE hot path on GB300 (one JSON line on stdout).
 
 A step is one full forward pass (range, histograms, tables, mapping) over one
-synthetic volume already resident in HBM.  The default workload is the 3-D
-fluorescence-like stack 64x512x512 (kernel 16x64x64, 256 bins, clip 0.02,
-adaptive range).  L2 is flushed (a 256 MiB write) between timed steps, outside
-the step's events.  Each pass is timed with CUDA events on the stream that
-launches it; the step time is the first-to-last event span.
+synthetic volume already resident in HBM.  The default workload (the headline)
+is the largest one-GPU configuration, the 4-D photoemission-like volume
+128x128x256x32 (kernel 32x32x32x8, 512 bins, clip 0.01, global range found on
+the device); the 3-D fluorescence-like stack 64x512x512 (kernel 16x64x64, 256
+bins, clip 0.02, adaptive range) and the 2-D image 512x512 are measured the
+same way and reported beside it.  L2 is flushed (a 256 MiB write) between
+timed steps, outside the step's events.  Each pass is timed with CUDA events on
+the stream that launches it; the step time is the first-to-last event span.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU oracle on this host
@@ -31,7 +34,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "MCLAHE Gvoxel/s & % HBM roofline; batched and fwd+bwd vs plain fwd"
-DEFAULT_WORKLOAD = "3d-fluorescence-64x512x512"
+DEFAULT_WORKLOAD = "4d-photoemission-128x128x256x32"
+EXTRA_WORKLOADS = ("3d-fluorescence-64x512x512", "2d-smooth-512x512")
 L2_FLUSH_BYTES = 256 << 20
 PEAK_FALLBACK_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal (context for the measured peak)
@@ -49,7 +53,7 @@ def pass_kernel(pass_name, info):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
@@ -64,6 +68,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and forward+backward forms")
     ap.add_argument("--form-steps", type=int, default=20)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="measure only the selected workload (not the other configurations)")
     return ap.parse_args()
 
 
@@ -193,9 +199,22 @@ def kernel_source_hash(pass_name):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, pass_name):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+# launch shapes that select the kernel variant of a pass
+VARIANT_KEYS = {
+    "range": ("hist_shares", "hist_walk", "hist_threads"),
+    "hist": ("hist_group", "hist_cluster", "hist_copies", "hist_shares", "hist_walk", "hist_threads"),
+    "map": ("map_chunks", "map_tma", "map_flat"),
+}
+
+
+def pass_variant(pass_name, info):
+    return {k: int(info[k]) for k in VARIANT_KEYS[pass_name]}
+
+
+def recorded_traffic(workload, pass_name, info):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source, the same kernel and the same launch shapes (else
+    None)."""
     path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.json")
     try:
         with open(path) as f:
@@ -203,6 +222,10 @@ def recorded_traffic(workload, pass_name):
     except Exception:
         return None
     if rec.get("source_sha") != kernel_source_hash(pass_name):
+        return None
+    if rec.get("kernel", "").split("<")[0] != pass_kernel(pass_name, info):
+        return None
+    if rec.get("shapes") != pass_variant(pass_name, info):
         return None
     return rec.get("bytes_per_launch")
 
@@ -254,18 +277,25 @@ def run_reference(args):
 
     oracle.build()
     clip = float(np.float32(w["clip_limit"]))
-    # bound the whole run to about two minutes: shrink the volume along dim 0
-    # (whole kernels) when K full-volume steps would take longer
+    # bound the whole run to about two minutes: shrink the volume to a leading
+    # block of whole kernels (dim 0 first, then dim 1, ...) when K full-volume
+    # steps would take longer
     t0 = time.perf_counter()
     oracle.mclahe(x, w["kernel"], w["n_bins"], clip, mode=int(w["adaptive"]))
     t_full = time.perf_counter() - t0
     sample = f"the whole {args.workload} volume per step"
     budget = 120.0 / max(args.steps + args.warmup, 1)
     if t_full > budget:
-        b0 = w["kernel"][0]
-        s0 = max(b0, int(w["shape"][0] * budget / t_full) // b0 * b0)
-        x = np.ascontiguousarray(x[:s0])
-        sample = f"leading {s0} of {w['shape'][0]} slices of the {args.workload} volume per step"
+        ext = list(w["shape"])
+        for d in range(len(ext)):
+            b = w["kernel"][d]
+            frac = budget / (t_full * np.prod(ext) / np.prod(w["shape"]))
+            ext[d] = max(b, int(ext[d] * frac) // b * b)
+            if t_full * np.prod(ext) / np.prod(w["shape"]) <= budget:
+                break
+        x = np.ascontiguousarray(x[tuple(slice(0, e) for e in ext)])
+        sample = (f"leading {'x'.join(str(e) for e in ext)} block (whole kernels) of the "
+                  f"{args.workload} volume per step")
     for _ in range(max(args.warmup, 0)):
         oracle.mclahe(x, w["kernel"], w["n_bins"], clip, mode=int(w["adaptive"]))
     t0 = time.perf_counter()
@@ -399,13 +429,28 @@ def measure_fwd_bwd(dev, steps, warmup):
             nat.mclahe_backward(op.plan, xs[v], gouts[v], wss[v], op.ws_bytes, clips[v:v + 1], None,
                                 gclip[v:v + 1], stream)
 
+    def bwd():   # the backward calls alone (upstream gradients already in gouts)
+        for v in range(B):
+            nat.mclahe_backward(op.plan, xs[v], gouts[v], wss[v], op.ws_bytes, clips[v:v + 1], None,
+                                gclip[v:v + 1], stream)
+
     ms_fwd = _time_steps(fwd, steps, warmup, stream)
     ms_fb = _time_steps(fwd_bwd, steps, warmup, stream)
+    ms_bwd = _time_steps(bwd, steps, warmup, stream)
     voxels = int(n)
+    peak, peak_kind = measured_peak_gbs()
+    bwd_bytes = 8 * voxels   # reads of the input and the upstream gradient
     out = {"workload": "fwd+bwd-8x64x256x256-learnable-clip", "voxels": voxels,
            "value": voxels / (ms_fb * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms_fb,
            "forward_ms": ms_fwd, "forward_value": voxels / (ms_fwd * 1e-3) / 1e9,
            "fwd_bwd_over_fwd": ms_fb / ms_fwd,
+           "backward_ms": ms_bwd,
+           "backward_roofline": {"bound": "hbm", "algorithmic_bytes": bwd_bytes,
+                                 "achieved": bwd_bytes / (ms_bwd * 1e-3) / 1e9, "peak": peak,
+                                 "unit": "GB/s", "frac": bwd_bytes / (ms_bwd * 1e-3) / 1e9 / peak,
+                                 "peak_kind": peak_kind,
+                                 "note": "8 mclahe_backward calls (k_gmax, k_adj, k_lutbwd, "
+                                         "k_clipgrad each), 8 B per voxel"},
            "grad_clip_finite": bool(torch.isfinite(gclip).all().item()),
            "data": "synthetic, drawn on the device (torch generators, seeds 2000+v, targets 3000+v)"}
     del xs, tgt, wss, outs, gouts
@@ -416,6 +461,147 @@ def measure_fwd_bwd(dev, steps, warmup):
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
+SHAPE_KEYS = ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk", "hist_threads",
+              "map_flat", "map_chunks", "map_tma", "tuned")
+
+
+class Workload:
+    """One workload on the device: its plan (autotuned or given shapes), input,
+    output, and the step and per-pass timings."""
+
+    def __init__(self, name, args, dev, rank, given_range=False):
+        import numpy as np
+        import torch
+
+        from paper_1906_11355_gb300 import synth
+        from paper_1906_11355_gb300.api import MCLAHE
+        from paper_1906_11355_gb300.dist import rank_seed
+
+        self.name = name
+        self.w = w = synth.WORKLOADS[name]
+        self.x_host = synth.make_volume(w["gen"], w["shape"], rank_seed(w["seed"], rank))
+        rng = None
+        if given_range:   # the data's own range, given to the plan (no range pass)
+            rng = (float(self.x_host.min()), float(self.x_host.max()))
+        self.given_range = rng
+        self.op = MCLAHE(w["shape"], w["kernel"], w["n_bins"], float(np.float32(w["clip_limit"])),
+                         adaptive=w["adaptive"], global_range=rng, device=dev)
+        self.x = torch.from_numpy(self.x_host).to(dev)
+        self.out = torch.empty_like(self.x)
+        self.voxels = int(np.prod(w["shape"]))
+        self.dev = dev
+
+    def tune(self, args):
+        import json as _json
+
+        from paper_1906_11355_gb300 import _native as nat
+
+        if args.shapes and self.name == args.workload:
+            self.op.set_shapes(**_json.loads(args.shapes))
+        elif not args.no_autotune:
+            self.op.autotune(self.x, self.out)   # timed on this volume, outside the timed region
+        self.info = nat.mclahe_plan_query(self.op.plan)
+        self.shapes = {k: v for k, v in self.info.items() if k in SHAPE_KEYS}
+        self.launches = {p: nat.mclahe_pass_launches(self.op.plan, p) for p in range(nat.MCLAHE_N_PASSES)}
+
+    def step_fn(self, args, stream):
+        from paper_1906_11355_gb300 import _native as nat
+
+        fwd = nat.mclahe_forward if args.no_graph else nat.mclahe_forward_graph
+        op, x, out = self.op, self.x, self.out
+
+        def step(e0, e1):
+            e0.record(stream)
+            fwd(op.plan, x, out, op.ws, op.ws_bytes, None, stream)
+            e1.record(stream)
+
+        return step
+
+    def time_passes(self, flush, stream, n):
+        """Mean time of each pass (an event between passes; L2 flushed first)."""
+        import torch
+
+        from paper_1906_11355_gb300 import _native as nat
+
+        passes = list(range(nat.MCLAHE_N_PASSES))
+        bd = [[torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)] for _ in range(n)]
+        op = self.op
+        for i in range(n):
+            flush.fill_(i & 0xFF)
+            bd[i][0].record(stream)
+            for p in passes:
+                nat.mclahe_forward_pass(op.plan, p, self.x, self.out, op.ws, op.ws_bytes, None, stream)
+                bd[i][p + 1].record(stream)
+        torch.cuda.synchronize(self.dev)
+        return {nat.PASS_NAMES[p]: sum(ev[p].elapsed_time(ev[p + 1]) for ev in bd) / n for p in passes}
+
+    def roofline(self, pass_ms):
+        from paper_1906_11355_gb300 import _native as nat
+
+        peak, peak_kind = measured_peak_gbs()
+        w = self.w
+        algo = algorithmic_bytes(self.info, w["adaptive"], self.given_range is not None)
+        kern = {k: v for k, v in pass_ms.items()
+                if k in ("range", "hist", "map") and self.launches[nat.PASS_NAMES.index(k)] > 0}
+        per_pass = {}
+        for k in kern:
+            ach = algo[k] / (pass_ms[k] * 1e-3) / 1e9
+            per_pass[k] = {"kernel": pass_kernel(k, self.info), "variant": pass_variant(k, self.info),
+                           "ms": pass_ms[k], "algorithmic_bytes": algo[k], "achieved": ach,
+                           "frac": ach / peak, "traffic": recorded_traffic(self.name, k, self.info)}
+        dom = max(kern, key=kern.get)
+        d = per_pass[dom]
+        return {"bound": "hbm", "kernel": d["kernel"], "variant": d["variant"],
+                "achieved": d["achieved"], "peak": peak, "unit": "GB/s", "frac": d["frac"],
+                "traffic": d["traffic"], "peak_kind": peak_kind, "algorithmic_bytes": d["algorithmic_bytes"],
+                "frac_of_nominal": d["achieved"] / NOMINAL_HBM_GBS}, per_pass
+
+    def config(self, args):
+        w = self.w
+        c = {"workload": self.name, "shape": list(w["shape"]), "kernel": list(w["kernel"]),
+             "n_bins": w["n_bins"], "clip_limit": w["clip_limit"],
+             "range": "adaptive" if w["adaptive"] else "global",
+             "l2": "flushed between steps (256 MiB write outside the step events)",
+             "launch_shapes": self.shapes,
+             "call": "mclahe_forward" if args.no_graph else "mclahe_forward_graph",
+             "voxels_per_gpu": self.voxels}
+        if self.given_range is not None:
+            c["range"] = "global, given to the plan (the data's own min and max; no range pass)"
+        return c
+
+    def release(self):
+        import torch
+
+        del self.x, self.out, self.op
+        torch.cuda.empty_cache()
+
+
+def measure_simple(wl, args, stream, flush, steps):
+    """A workload beside the headline: step time (events, L2 flushed between
+    steps), per-pass times and rooflines."""
+    import torch
+
+    step = wl.step_fn(args, stream)
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        step(*ev[i])
+    torch.cuda.synchronize(wl.dev)
+    ms_l = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(ms_l) / steps
+    pass_ms = wl.time_passes(flush, stream, min(steps, 50))
+    roof, per_pass = wl.roofline(pass_ms)
+    return {"value": wl.voxels / (ms * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms,
+            "ms_per_step_median": float(sorted(ms_l)[len(ms_l) // 2]), "steps": steps,
+            "hbm_roofline_frac_whole_step": 12 * wl.voxels / (ms * 1e-3) / 1e9 / roof["peak"],
+            "config": wl.config(args), "passes_ms": pass_ms, "roofline": roof,
+            "roofline_per_pass": per_pass}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -431,47 +617,17 @@ def run_native(args):
 
     from paper_1906_11355_gb300 import _native as nat
     from paper_1906_11355_gb300 import build as nbuild
-    from paper_1906_11355_gb300 import synth
-    from paper_1906_11355_gb300.api import MCLAHE
+    from paper_1906_11355_gb300.dist import max_over_ranks
 
     nbuild.build()
     nat.load()
-    w = synth.WORKLOADS[args.workload]
-    from paper_1906_11355_gb300.dist import max_over_ranks, rank_seed
-
-    x_host = synth.make_volume(w["gen"], w["shape"], rank_seed(w["seed"], rank))
-    op = MCLAHE(w["shape"], w["kernel"], w["n_bins"], float(np.float32(w["clip_limit"])),
-                adaptive=w["adaptive"], device=dev)
-    x = torch.from_numpy(x_host).to(dev)
-    out = torch.empty_like(x)
-    if args.shapes:
-        op.set_shapes(**json.loads(args.shapes))
-    elif not args.no_autotune:
-        op.autotune(x, out)   # launch shapes timed on this volume (outside the timed region)
-    shapes = {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
-              if k in ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk", "hist_threads", "map_flat",
-                       "map_chunks", "map_tma", "tuned")}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    passes = list(range(nat.MCLAHE_N_PASSES))
-    launches = {p: nat.mclahe_pass_launches(op.plan, p) for p in passes}
 
-    # a step: one forward call (all passes; by default replayed from the CUDA
-    # graph mclahe_forward_graph caches) between two events
-    fwd = nat.mclahe_forward if args.no_graph else nat.mclahe_forward_graph
-
-    def step(e0, e1):
-        e0.record(stream)
-        fwd(op.plan, x, out, op.ws, op.ws_bytes, None, stream)
-        e1.record(stream)
-
-    # the per-pass breakdown: each pass between events (an extra loop, untimed
-    # for the headline)
-    def step_passes(evs):
-        evs[0].record(stream)
-        for p in passes:
-            nat.mclahe_forward_pass(op.plan, p, x, out, op.ws, op.ws_bytes, None, stream)
-            evs[p + 1].record(stream)
+    wl = Workload(args.workload, args, dev, rank)
+    wl.tune(args)
+    op, x, out = wl.op, wl.x, wl.out
+    step = wl.step_fn(args, stream)
 
     for _ in range(args.warmup):
         flush.fill_(1)
@@ -497,24 +653,17 @@ def run_native(args):
     sampler.stop()
 
     step_ms = [a.elapsed_time(b) for a, b in events]
-    n_bd = min(args.steps, 50)
-    bd = [[torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)] for _ in range(n_bd)]
-    for i in range(n_bd):
-        flush.fill_(i & 0xFF)
-        step_passes(bd[i])
-    torch.cuda.synchronize(dev)
-    pass_ms = {nat.PASS_NAMES[p]: sum(ev[p].elapsed_time(ev[p + 1]) for ev in bd) / n_bd
-               for p in passes}
+    pass_ms = wl.time_passes(flush, stream, min(args.steps, 50))
     ms = sum(step_ms) / args.steps
     ms_median = float(sorted(step_ms)[len(step_ms) // 2])
     ms = max_over_ranks(ms, device=dev)   # the slowest rank sets the whole-job time
-    voxels = int(np.prod(w["shape"]))
+    voxels = wl.voxels
     value = voxels * world / (ms * 1e-3) / 1e9
 
     # end to end through the public API: pinned host -> device, forward, device -> host
     e2e = None
     if rank == 0 or world > 1:
-        h_in = torch.from_numpy(x_host).pin_memory()
+        h_in = torch.from_numpy(wl.x_host).pin_memory()
         h_out = torch.empty(h_in.shape, dtype=torch.float32).pin_memory()
         for _ in range(3):
             op.forward(h_in.to(dev, non_blocking=True), out=out)
@@ -533,6 +682,7 @@ def run_native(args):
         e2e = {"value": voxels * world / (e2e_ms * 1e-3) / 1e9, "unit": "Gvoxel/s",
                "h2d_bytes_per_step": int(h_in.numel() * 4), "d2h_bytes_per_step": int(h_out.numel() * 4),
                "ms_per_step": e2e_ms}
+        del h_in, h_out
 
     if world > 1:
         torch.distributed.barrier()
@@ -540,24 +690,35 @@ def run_native(args):
         torch.distributed.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel
-    peak, peak_kind = measured_peak_gbs()
-    info = nat.mclahe_plan_query(op.plan)   # launch shapes after autotuning
-    algo = algorithmic_bytes(info, w["adaptive"], False)
-    kern = {k: v for k, v in pass_ms.items()
-            if k in ("range", "hist", "map") and launches[nat.PASS_NAMES.index(k)] > 0}
-    dom = max(kern, key=kern.get)
-    achieved = algo[dom] / (pass_ms[dom] * 1e-3) / 1e9
-    traffic = recorded_traffic(args.workload, dom)
-    roofline = {"bound": "hbm", "kernel": pass_kernel(dom, info), "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "peak_kind": peak_kind, "algorithmic_bytes": algo[dom],
-                "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    roofline, per_pass = wl.roofline(pass_ms)
     whole = 12 * voxels / (ms * 1e-3) / 1e9    # 2 input reads + 1 output write
+    config = wl.config(args)
+    x_host = wl.x_host
+    wname = wl.w
+    gpu_launches = int(sum(wl.launches.values()) * args.steps)
+    wl.release()
+
+    # the other configurations, and the headline volume with its range given
+    extra = None
+    if not args.no_extra and world == 1:
+        extra = {}
+        if not wname["adaptive"]:
+            g = Workload(args.workload, args, dev, rank, given_range=True)
+            g.tune(args)
+            extra[args.workload + "+given-range"] = measure_simple(g, args, stream, flush,
+                                                                   min(args.steps, 2000))
+            g.release()
+        for name in EXTRA_WORKLOADS:
+            if name == args.workload:
+                continue
+            e = Workload(name, args, dev, rank)
+            e.tune(args)
+            extra[name] = measure_simple(e, args, stream, flush, min(args.steps, 2000))
+            e.release()
 
     cpu = None
     if not args.no_cpu_baseline:
-        rate, reps, el, cores, single = oracle_rate(x_host, w)
+        rate, reps, el, cores, single = oracle_rate(x_host, wname)
         cpu = {"value": rate, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
                "sample": f"whole {args.workload} volume x{reps} ({el:.1f} s, FP64, OpenMP)",
                "single_thread": single}
@@ -571,21 +732,17 @@ def run_native(args):
         "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "shape": list(w["shape"]), "kernel": list(w["kernel"]),
-                   "n_bins": w["n_bins"], "clip_limit": w["clip_limit"],
-                   "range": "adaptive" if w["adaptive"] else "global",
-                   "l2": "flushed between steps (256 MiB write outside the step events)",
-                   "launch_shapes": shapes,
-                   "call": "mclahe_forward" if args.no_graph else "mclahe_forward_graph",
-                   "voxels_per_gpu": voxels},
-        "hbm_roofline_frac_whole_step": whole / peak,
+        "config": config,
+        "hbm_roofline_frac_whole_step": whole / roofline["peak"],
         "ms_per_step_median": ms_median,
         "passes_ms": pass_ms,
         "roofline": roofline,
+        "roofline_per_pass": per_pass,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": int(sum(launches.values()) * args.steps),
+        "gpu_launches": gpu_launches,
         "clocks": sampler.summary(t0, t1),
+        "workloads": extra,
         "forms": forms,
     }
     print(json.dumps(line))

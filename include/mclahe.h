@@ -272,6 +272,26 @@ MCLAHE_API mclahe_status mclahe_batch(int n_vol, const mclahe_plan_t *plans, con
 MCLAHE_API size_t mclahe_batch_workspace_bytes(int n_vol, const mclahe_plan_t *plans);
 
 /*
+ * mclahe_batch_set_wait -- the bounded waits of mclahe_batch's persistent
+ * launches (no counterpart in the paper; failure detection).  A tile that
+ * depends on another phase of its volume polls that volume's ready counter;
+ * after max_polls polls (with a growing back-off of up to about 1 us each) it
+ * gives up, records MCLAHE_ERR_TIMEOUT in the batch status word (read back by
+ * mclahe_sync_status on the batch workspace) and every later wait of the
+ * launch returns at once, so the launch always ends.  The results of a launch
+ * that gave up are undefined.
+ *   max_polls    polls before a wait gives up; 0 restores the default (2^22).
+ *   unreachable  0 in normal use.  Non-zero raises every wait's target above
+ *                any value the counter can reach, so that the first wait gives
+ *                up after max_polls polls: this tests the timeout path without
+ *                faulting or hanging the device.
+ * Host-side setting for the process, applied to mclahe_batch calls made after
+ * it (a cached batch graph records the setting it was captured with).  Always
+ * returns MCLAHE_OK.
+ */
+MCLAHE_API mclahe_status mclahe_batch_set_wait(uint32_t max_polls, int unreachable);
+
+/*
  * mclahe_autotune -- time the candidate launch shapes of the plan's passes on
  * the given buffers (which it overwrites) and keep the fastest in the plan.
  * Results are cached per (D, kernel size, n_bins, range mode) for the process.
@@ -322,12 +342,16 @@ MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist
  *   d_in, d_out, d_clip, stream   as for mclahe_forward.
  * The workspace comes from one array of MCLAHE_NOALLOC_SCRATCH_BYTES built into
  * the library, which every GPU that uses the library keeps until the process
- * exits.  This call allocates nothing.  The first call on each device looks up
- * the array's device address (with that device current) and caches it; make
- * that first call before any stream capture.  All calls share the array and it
- * keeps the last call's contents (the parts that must start at zero are cleared
- * by every call), so calls that overlap on the GPU race with each other; run
- * them on one stream or otherwise one after another.
+ * exits.  This call allocates nothing.  Every call looks up the array's device
+ * address on the current device (a host-side lookup, so a reset device context
+ * is picked up); the first call on a device may load the library's device code,
+ * so make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (the parts that must start at zero are
+ * cleared by every call), so calls that overlap on the GPU race with each other;
+ * run them on one stream or otherwise one after another.
+ * Errors found by device code (a bounded wait that gave up) are recorded in the
+ * status word of the built-in array, like mclahe_forward's in its workspace;
+ * read and clear it with mclahe_noalloc_sync_status.
  * Returns MCLAHE_ERR_UNSUPPORTED when the plan's forward workspace (the offset
  * ws_scratch of mclahe_plan_info) exceeds MCLAHE_NOALLOC_SCRATCH_BYTES,
  * MCLAHE_ERR_INVALID_ARG for NULL, aliased or misaligned pointers, and
@@ -335,6 +359,13 @@ MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist
  */
 MCLAHE_API mclahe_status mclahe_forward_noalloc(mclahe_plan_t plan, const float *d_in, float *d_out,
                                                 const float *d_clip, mclahe_stream_t stream);
+
+/* mclahe_noalloc_sync_status -- mclahe_sync_status for the built-in array of
+ * mclahe_forward_noalloc on the current device (no counterpart in the paper):
+ * synchronise `stream`, then read and clear the array's status word.  Allocates
+ * nothing.  Returns MCLAHE_OK, the error device code recorded, or
+ * MCLAHE_ERR_CUDA if the lookup or the copy fails. */
+MCLAHE_API mclahe_status mclahe_noalloc_sync_status(mclahe_stream_t stream);
 
 /* Synchronise `stream`, then read and clear the device status word of the
  * workspace.  Returns MCLAHE_OK or the error device code recorded. */

@@ -33,7 +33,8 @@ EXPORTS = (
     "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
-    "mclahe_plan_set_shapes", "mclahe_forward_graph",
+    "mclahe_plan_set_shapes", "mclahe_forward_graph", "mclahe_noalloc_sync_status",
+    "mclahe_batch_set_wait",
 )
 
 MCLAHE_NOALLOC_SCRATCH_BYTES = 8 << 20
@@ -126,6 +127,10 @@ def load(path: str = LIB_PATH):
         lib.mclahe_pass_launches.restype = ctypes.c_int
         lib.mclahe_forward_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.mclahe_forward_noalloc.restype = ctypes.c_int
+        lib.mclahe_noalloc_sync_status.argtypes = [vp]
+        lib.mclahe_noalloc_sync_status.restype = ctypes.c_int
+        lib.mclahe_batch_set_wait.argtypes = [ctypes.c_uint32, ctypes.c_int]
+        lib.mclahe_batch_set_wait.restype = ctypes.c_int
         lib.mclahe_plan_set_shapes.argtypes = [vp] + [ctypes.c_int32] * 9
         lib.mclahe_plan_set_shapes.restype = ctypes.c_int
         lib.mclahe_version.argtypes = []
@@ -242,6 +247,11 @@ def mclahe_forward_noalloc(plan, d_in, d_out, d_clip=None, stream=None):
     _check(st, "mclahe_forward_noalloc")
 
 
+def mclahe_noalloc_sync_status(stream=None) -> int:
+    """Read and clear the status word of the built-in array of mclahe_forward_noalloc."""
+    return int(load().mclahe_noalloc_sync_status(_stream(stream)))
+
+
 def mclahe_forward_pass(plan, pass_, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
     st = load().mclahe_forward_pass(plan.handle, int(pass_), _ptr(d_in), _ptr(d_out), _ptr(d_ws),
                                     int(ws_bytes), _ptr(d_clip), _stream(stream))
@@ -276,6 +286,13 @@ def mclahe_batch(plans, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None, u
     st = load().mclahe_batch(n, hs, _ptr_array(d_in), _ptr_array(d_out), _ptr(d_ws), int(ws_bytes),
                              _ptr(d_clip), _stream(stream), 1 if use_graph else 0)
     _check(st, "mclahe_batch")
+
+
+def mclahe_batch_set_wait(max_polls=0, unreachable=False):
+    """Polls before a batch wait gives up (0: default); unreachable=True raises every
+    wait target out of reach (tests of the timeout path only)."""
+    _check(load().mclahe_batch_set_wait(int(max_polls), 1 if unreachable else 0),
+           "mclahe_batch_set_wait")
 
 
 def mclahe_autotune(plan, d_in, d_out, d_ws, ws_bytes, stream=None):

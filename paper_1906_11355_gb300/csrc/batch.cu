@@ -28,6 +28,7 @@
 // the memset of the control block and all launches are captured once into a
 // CUDA graph, cached per (plans, pointers), and replayed.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <new>
@@ -45,6 +46,11 @@ namespace mclahe {
 namespace {
 
 size_t align_ws(size_t x) { return (x + kWsAlign - 1) / kWsAlign * kWsAlign; }
+
+// mclahe_batch_set_wait: polls before a wait gives up, and whether every wait
+// target is raised out of reach (testing of the timeout path only)
+std::atomic<uint32_t> g_wait_polls{kWaitSpins};
+std::atomic<uint32_t> g_wait_unreachable{0};
 
 // Control block: status (16 B), then per launch group a work counter, then
 // per volume 2 done counters and 2 range keys.
@@ -114,6 +120,8 @@ mclahe_status enqueue_batch(int n_vol, const mclahe_plan_t *plans, const float *
         bp->n_vol = nv;
         bp->next = reinterpret_cast<unsigned long long *>(ws + L.next + 8 * size_t(launch));
         bp->status = reinterpret_cast<uint32_t *>(ws);
+        bp->wait_polls = g_wait_polls.load();
+        bp->target_bias = g_wait_unreachable.load() ? 0x80000000u : 0u;
         // cluster size: the most common histogram cluster size of the group
         int C = 1;
         {
@@ -290,9 +298,18 @@ mclahe_status mclahe_batch(int n_vol, const mclahe_plan_t *plans, const float *c
     }
     key.ptrs.push_back(d_ws);
     key.ptrs.push_back(d_clip);
+    // the wait setting is captured into the graph's launch parameters
+    key.ptrs.push_back(reinterpret_cast<const void *>(uintptr_t(g_wait_polls.load())));
+    key.ptrs.push_back(reinterpret_cast<const void *>(uintptr_t(g_wait_unreachable.load())));
     return replay_cached(key, st, [&](cudaStream_t cap) {
         return enqueue_batch(n_vol, plans, d_in, d_out, ws, d_clip, cap);
     });
+}
+
+mclahe_status mclahe_batch_set_wait(uint32_t max_polls, int unreachable) {
+    g_wait_polls.store(max_polls ? max_polls : kWaitSpins);
+    g_wait_unreachable.store(unreachable ? 1u : 0u);
+    return MCLAHE_OK;
 }
 
 mclahe_status mclahe_forward_graph(mclahe_plan_t p, const float *d_in, float *d_out, void *d_ws,

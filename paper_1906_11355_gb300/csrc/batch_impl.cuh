@@ -11,7 +11,7 @@ namespace mclahe {
 
 constexpr int kGroupVol = 64;                 // volumes per persistent launch
 constexpr int kMaxStage = 3 * kGroupVol;
-constexpr uint32_t kWaitSpins = 1u << 22;     // ~ seconds with the back-off below
+constexpr uint32_t kWaitSpins = 1u << 22;     // default polls: ~ seconds with the back-off below
 
 struct BVol {
     Geom g;
@@ -34,6 +34,9 @@ struct BParams {
     unsigned long long *next;   // work counter
     uint32_t *done;             // per volume: range tiles done, kernel tiles done
     uint32_t *status;           // batch status word
+    uint32_t wait_polls;        // polls before a wait gives up
+    uint32_t target_bias;       // added to every wait target (0; non-zero only to test the
+                                // timeout path: no counter reaches the raised target)
     int64_t stage_start[kMaxStage + 1];
     int32_t stage_kind[kMaxStage];   // 0 range, 1 kernel, 2 cell
     int32_t stage_vol[kMaxStage];
@@ -42,8 +45,11 @@ struct BParams {
 
 static_assert(sizeof(BParams) <= 32000, "batch parameters must fit the kernel parameter space");
 
-// Thread 0 waits (bounded) until *ctr >= target; then the block proceeds.
-__device__ __forceinline__ void wait_ready(const uint32_t *ctr, uint32_t target, uint32_t *status) {
+// Thread 0 waits (bounded: at most `polls` polls) until *ctr >= target; then
+// the block proceeds.  A wait that gives up records MCLAHE_ERR_TIMEOUT, and
+// every later wait of the launch returns at once.
+__device__ __forceinline__ void wait_ready(const uint32_t *ctr, uint32_t target, uint32_t *status,
+                                           uint32_t polls) {
     if (threadIdx.x == 0) {
         uint32_t spins = 0, ns = 32;
         for (;;) {
@@ -51,7 +57,7 @@ __device__ __forceinline__ void wait_ready(const uint32_t *ctr, uint32_t target,
             uint32_t v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
             if (v >= target) break;
-            if (++spins > kWaitSpins) {
+            if (++spins > polls) {
                 atomicCAS(status, 0u, uint32_t(MCLAHE_ERR_TIMEOUT));
                 break;
             }
@@ -145,13 +151,15 @@ __global__ void __launch_bounds__(256, D <= 2 ? 3 : ((D >= 4 && ADAPTIVE) ? 1 : 
                 signal_done(&bp.done[2 * vi]);
                 break;
             case 1:
-                if (V.n_range > 0) wait_ready(&bp.done[2 * vi], uint32_t(V.n_range * C), bp.status);
+                if (V.n_range > 0) wait_ready(&bp.done[2 * vi], uint32_t(V.n_range * C) + bp.target_bias, bp.status,
+                                           bp.wait_polls);
                 hist_group<D, ADAPTIVE>(V.g, V.in, V.keys, V.clip, V.hist, V.lut, V.lo, V.scale, idx,
                                         V.G, V.R, smem);
                 if (rank == 0) signal_done(&bp.done[2 * vi + 1]);
                 break;
             default: {
-                wait_ready(&bp.done[2 * vi + 1], uint32_t(V.n_hist), bp.status);
+                wait_ready(&bp.done[2 * vi + 1], uint32_t(V.n_hist) + bp.target_bias, bp.status,
+                           bp.wait_polls);
                 const int64_t cell = idx / V.mgroups;
                 const int grp = int(idx - cell * V.mgroups);
                 map_cell<D, ADAPTIVE, true, false>(V.g, V.in, V.out, V.lut, V.lo, V.scale, cell,

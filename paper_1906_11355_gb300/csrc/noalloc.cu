@@ -11,12 +11,16 @@
 //
 // The array lives in device global memory; every GPU on which the library is
 // used holds MCLAHE_NOALLOC_SCRATCH_BYTES of it until the process exits.  Host
-// code cannot use the array's name as a device address, so the first call on
-// each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it; that first call should therefore come before any
-// stream capture.  All calls share the one array, so calls whose work overlaps
-// on the GPU (other streams, other threads) race; the forward pass clears the
-// parts that must start at zero on every call.
+// code cannot use the array's name as a device address, so every call looks
+// the address up with cudaGetSymbolAddress on the current device (a host-side
+// lookup; the first one on a device may load the library's device code, so
+// that first call should come before any stream capture).  Looking it up per
+// call keeps the address right even if the device's context was reset and the
+// module reloaded.  All calls share the one array, so calls whose work
+// overlaps on the GPU (other streams, other threads) race; the forward pass
+// clears the parts that must start at zero on every call.  The array's first
+// word is the status word of its workspace: mclahe_noalloc_sync_status reads
+// and clears it.
 #include <mutex>
 
 #include "mclahe_internal.cuh"
@@ -26,24 +30,15 @@ namespace mclahe {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MCLAHE_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-unsigned char *g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device.
 cudaError_t scratch_address(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 }  // namespace
@@ -64,4 +59,11 @@ extern "C" mclahe_status mclahe_forward_noalloc(mclahe_plan_t p, const float *d_
     unsigned char *ws = nullptr;
     if (scratch_address(&ws) != cudaSuccess) return MCLAHE_ERR_CUDA;
     return forward_impl(*p, d_in, d_out, ws, d_clip, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" mclahe_status mclahe_noalloc_sync_status(mclahe_stream_t stream) {
+    unsigned char *ws = nullptr;
+    if (scratch_address(&ws) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    // the status word sits at offset 0 of every plan's workspace layout
+    return mclahe_sync_status(ws, stream);
 }

@@ -29,7 +29,7 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["value"] > 0 and d["unit"] == "Gvoxel/s" and d["higher_is_better"] is True
     assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 1, 3)
-    assert d["config"]["workload"] == "3d-fluorescence-64x512x512"
+    assert d["config"]["workload"] == "4d-photoemission-128x128x256x32"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]

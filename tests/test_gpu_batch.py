@@ -126,3 +126,43 @@ def test_autotune_keeps_results_exact(torch_cuda, orc):
     want, aux = orc.mclahe(x, (8, 16, 16), 256, float(np.float32(0.02)), mode=1, full=True)
     np.testing.assert_array_equal(op.histograms().cpu().numpy(), aux["hist"].astype(np.int64))
     assert np.abs(out.cpu().numpy() - want).max() <= 1e-5
+
+
+def test_batch_wait_that_gives_up_reports_timeout_and_the_launch_ends(torch_cuda, orc):
+    """Failure detection of the persistent launches: every wait target is raised
+    out of reach (mclahe_batch_set_wait's test switch), so the first wait on a
+    ready counter polls a short while, gives up and records MCLAHE_ERR_TIMEOUT;
+    the later waits then return at once and the launch ends.  Nothing faults or
+    hangs: the status is read back on the host, and the next normal call on the
+    same workspace is correct."""
+    import time
+
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHEBatch
+
+    specs = _specs()[:7]   # 2-D global (range tiles), 3-D adaptive and 4-D volumes
+    xs_h = _inputs(specs, 21)
+    xs = [torch.from_numpy(x).cuda() for x in xs_h]
+    batch = MCLAHEBatch(specs)
+    outs = [torch.empty_like(x) for x in xs]
+    torch.cuda.synchronize()
+    nat.mclahe_batch_set_wait(2000, unreachable=True)
+    try:
+        t0 = time.time()
+        batch.forward(xs, outs=outs, use_graph=False)
+        status = nat.mclahe_sync_status(batch.ws)
+        elapsed = time.time() - t0
+    finally:
+        nat.mclahe_batch_set_wait(0, unreachable=False)
+    assert status == nat.MCLAHE_ERR_TIMEOUT
+    assert elapsed < 30.0
+    assert nat.mclahe_sync_status(batch.ws) == nat.MCLAHE_OK   # reading it cleared it
+    for use_graph in (False, True):
+        batch.forward(xs, outs=outs, use_graph=use_graph)
+        torch.cuda.synchronize()
+        assert nat.mclahe_sync_status(batch.ws) == nat.MCLAHE_OK
+        for xh, s, out in zip(xs_h, specs, outs):
+            want = orc.mclahe(xh, s["kernel"], s["n_bins"], s["clip_limit"], mode=int(s["adaptive"]),
+                              range_=s.get("global_range"))
+            assert np.abs(out.cpu().numpy().astype(np.float64) - want).max() <= 1e-5, s

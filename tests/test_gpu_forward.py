@@ -2,8 +2,11 @@
 
 Histograms and ranges must match bit for bit, mapping tables to 1e-6 and the
 output to 1e-5 max-abs (the output lies in [0, 1]).  Small cases span several
-kernels and ragged tails in 1-4 dimensions; the workload cases run the full
-synthetic volumes in the launch configuration the benchmark times."""
+kernels and ragged tails in 1-4 dimensions.  The workload cases run the full
+synthetic volumes after mclahe_autotune has picked the launch shapes, which is
+what the benchmark does before it times them, and then under every mapping
+walk (per-cell grid, flat persistent grid, TMA tiles) with one and several
+CTAs per cell."""
 import numpy as np
 import pytest
 
@@ -277,10 +280,77 @@ def test_device_clip_overrides_plan_and_is_deterministic(torch_cuda, orc):
 WORKLOADS = ["2d-smooth-512x512", "3d-fluorescence-64x512x512", "4d-photoemission-128x128x256x32"]
 
 
-@pytest.mark.parametrize("name", WORKLOADS)
-def test_workload_full_size(torch_cuda, orc, name):
+@pytest.fixture(scope="module")
+def workload_cache(orc):
+    """Each full-size workload volume and its oracle result, computed once."""
     from paper_1906_11355_gb300 import synth
 
-    w = synth.WORKLOADS[name]
-    x = synth.make_volume(w["gen"], w["shape"], w["seed"])
-    run_case(torch_cuda, orc, x, w["kernel"], w["n_bins"], w["clip_limit"], w["adaptive"])
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            w = synth.WORKLOADS[name]
+            x = synth.make_volume(w["gen"], w["shape"], w["seed"])
+            want, aux = orc.mclahe(x, w["kernel"], w["n_bins"], f32(w["clip_limit"]),
+                                   mode=int(w["adaptive"]), full=True)
+            cache.clear()   # one full-size volume held at a time
+            cache[name] = (w, x, want, aux)
+        return cache[name]
+
+    return get
+
+
+def check_full(torch, op, xd, want, aux, out=None, graph=False):
+    out = op.forward(xd, out=out, graph=graph)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(op.histograms().cpu().numpy(), aux["hist"].astype(np.int64))
+    lo, sc = (t.cpu().numpy() for t in op.ranges())
+    np.testing.assert_array_equal(lo, aux["lo"])
+    np.testing.assert_array_equal(sc, aux["scale"])
+    assert np.abs(op.tables().cpu().numpy().astype(np.float64) - aux["lut"]).max() <= LUT_TOL
+    err = np.abs(out.cpu().numpy().astype(np.float64) - want).max()
+    assert err <= OUT_TOL, f"max abs error {err} with shapes {op.shapes()}"
+    return out
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_workload_full_size_autotuned(torch_cuda, workload_cache, name):
+    """The full volume with the launch shapes mclahe_autotune picks (the benchmark's
+    configuration), through mclahe_forward and the graph-replayed mclahe_forward_graph."""
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    w, x, want, aux = workload_cache(name)
+    op = MCLAHE(x.shape, w["kernel"], w["n_bins"], f32(w["clip_limit"]), w["adaptive"])
+    xd = torch_cuda.from_numpy(x).cuda()
+    out = torch_cuda.empty_like(xd)
+    op.autotune(xd, out)
+    check_full(torch_cuda, op, xd, want, aux, out=out)
+    out.fill_(-1.0)
+    check_full(torch_cuda, op, xd, want, aux, out=out, graph=True)
+
+
+def _map_walks(name, tuned):
+    walks = [dict(map_flat=0, map_tma=0, map_chunks=1), dict(map_flat=1, map_tma=0, map_chunks=1),
+             dict(map_flat=0, map_tma=0, map_chunks=4), dict(map_flat=1, map_tma=0, map_chunks=32)]
+    if name != "2d-smooth-512x512":
+        walks += [dict(map_flat=0, map_tma=1, map_chunks=1), dict(map_flat=0, map_tma=1, map_chunks=4)]
+    if tuned not in walks:
+        walks.append(tuned)
+    return walks
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_workload_full_size_every_mapping_walk(torch_cuda, workload_cache, name):
+    """The full volume under every mapping walk, with the autotuned histogram shapes."""
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    w, x, want, aux = workload_cache(name)
+    op = MCLAHE(x.shape, w["kernel"], w["n_bins"], f32(w["clip_limit"]), w["adaptive"])
+    xd = torch_cuda.from_numpy(x).cuda()
+    out = torch_cuda.empty_like(xd)
+    op.autotune(xd, out)
+    tuned = op.shapes()
+    for walk in _map_walks(name, {k: tuned[k] for k in ("map_flat", "map_tma", "map_chunks")}):
+        op.set_shapes(**{**tuned, **walk})
+        out.fill_(-1.0)
+        check_full(torch_cuda, op, xd, want, aux, out=out)

@@ -60,6 +60,10 @@ def test_noalloc_matches_forward_on_two_calls_in_a_row(env, shape, ks, nb, clip,
         torch.cuda.synchronize()
         err = (got - want).abs().max().item()
         assert err <= TOL, f"call {call}: max abs difference {err}"
+    # no device code recorded an error in the built-in array's status word, and
+    # reading it cleared it
+    assert nat.mclahe_noalloc_sync_status() == nat.MCLAHE_OK
+    assert nat.mclahe_noalloc_sync_status() == nat.MCLAHE_OK
 
 
 def test_noalloc_rejects_plans_beyond_its_scratch(env):

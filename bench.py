@@ -191,7 +191,7 @@ def kernel_source_hash(pass_name):
     traffic is only reported while this matches)."""
     hist = ("k_hist.cu", "k_hist_tma.cu", "k_hist_lsu.cu", "k_hist_impl.cuh", "hist_impl.cuh", "tma.cuh")
     files = {"range": ("k_range.cu",) + hist, "hist": hist,
-             "map": ("k_map.cu", "map_impl.cuh", "tma.cuh")}[pass_name]
+             "map": ("k_map.cu", "k_map_impl.cuh", "map_impl.cuh", "tma.cuh")}[pass_name]
     h = hashlib.sha256()
     for f in files + ("mclahe_internal.cuh",):
         with open(os.path.join(ROOT, "paper_1906_11355_gb300", "csrc", f), "rb") as fh:
@@ -602,6 +602,77 @@ def measure_simple(wl, args, stream, flush, steps):
             "roofline_per_pass": per_pass}
 
 
+TYPED_WORKLOADS = (("3d-fluorescence-64x512x512", "u16"), ("4d-photoemission-128x128x256x32", "u8"))
+
+
+def measure_typed(name, dtype, args, dev, stream, flush, steps):
+    """A workload read in its native integer type (mclahe_forward_typed): uint16
+    fluorescence counts, uint8 photoemission counts.  Launch shapes are tuned on
+    the float32 volume of the same values; bytes per voxel: the element size for
+    each input read (range pass under a global range, histogram, mapping) plus
+    4 for the output."""
+    import numpy as np
+    import torch
+
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300 import synth
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    w = synth.WORKLOADS[name]
+    if dtype == "u16":
+        xi = synth.fluorescence_u16(w["shape"], seed=w["seed"])
+        xd = torch.from_numpy(xi.view(np.int16)).to(dev)
+        code, esize = nat.MCLAHE_U16, 2
+    else:
+        xf = synth.make_volume(w["gen"], w["shape"], w["seed"])
+        assert xf.min() >= 0 and xf.max() <= 255 and np.array_equal(xf, np.round(xf))
+        xi = xf.astype(np.uint8)
+        xd = torch.from_numpy(xi).to(dev)
+        code, esize = nat.MCLAHE_U8, 1
+    op = MCLAHE(w["shape"], w["kernel"], w["n_bins"], float(np.float32(w["clip_limit"])),
+                adaptive=w["adaptive"], device=dev)
+    out = torch.empty(w["shape"], dtype=torch.float32, device=dev)
+    if not args.no_autotune:
+        xfl = torch.from_numpy(xi.astype(np.float32)).to(dev)
+        op.autotune(xfl, out)
+        del xfl
+    voxels = int(np.prod(w["shape"]))
+
+    def step(e0, e1):
+        e0.record(stream)
+        nat.mclahe_forward_typed(op.plan, code, xd, out, op.ws, op.ws_bytes, None, stream)
+        e1.record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        step(*ev[i])
+    torch.cuda.synchronize(dev)
+    ms_l = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(ms_l) / steps
+    reads = 3 if not w["adaptive"] else 2
+    step_bytes = voxels * (reads * esize + 4)
+    peak, peak_kind = measured_peak_gbs()
+    ach = step_bytes / (ms * 1e-3) / 1e9
+    res = {"value": voxels / (ms * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms,
+           "ms_per_step_median": float(sorted(ms_l)[len(ms_l) // 2]), "steps": steps,
+           "dtype": dtype, "call": "mclahe_forward_typed",
+           "config": {"workload": f"{name}-{dtype}", "shape": list(w["shape"]), "kernel": list(w["kernel"]),
+                      "n_bins": w["n_bins"], "clip_limit": w["clip_limit"],
+                      "range": "adaptive" if w["adaptive"] else "global", "input": dtype,
+                      "launch_shapes": {k: v for k, v in nat.mclahe_plan_query(op.plan).items()
+                                        if k in SHAPE_KEYS}},
+           "roofline_whole_step": {"bound": "hbm", "bytes_per_voxel": reads * esize + 4,
+                                   "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                   "peak_kind": peak_kind}}
+    del xd, out, op
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -715,6 +786,8 @@ def run_native(args):
             e.tune(args)
             extra[name] = measure_simple(e, args, stream, flush, min(args.steps, 2000))
             e.release()
+        for name, dt in TYPED_WORKLOADS:
+            extra[f"{name}-{dt}"] = measure_typed(name, dt, args, dev, stream, flush, min(args.steps, 2000))
 
     cpu = None
     if not args.no_cpu_baseline:

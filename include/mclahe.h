@@ -194,6 +194,34 @@ MCLAHE_API mclahe_status mclahe_forward_graph(mclahe_plan_t plan, const float *d
                                               void *d_ws, size_t ws_bytes, const float *d_clip,
                                               mclahe_stream_t stream);
 
+/* Element types of an input volume (mclahe_forward_typed). */
+typedef enum {
+    MCLAHE_F32 = 0,   /* float32 */
+    MCLAHE_U16 = 1,   /* uint16: intensity = the integer (exact in fp32) */
+    MCLAHE_U8 = 2     /* uint8: intensity = the integer */
+} mclahe_dtype;
+
+/*
+ * mclahe_forward_typed -- mclahe_forward for a volume stored as float32,
+ * uint16 or uint8 (Algorithm 1; Sec. III.B-III.D).  The paper's fluorescence
+ * data are 8-bit (Sec. IV.B) and detectors commonly write 16-bit counts;
+ * reading them as they are moves 2 or 1 bytes per voxel per pass instead of 4.
+ * An integer voxel's intensity is the integer itself, converted to fp32
+ * (exactly), so the output, histograms, ranges and tables equal those of
+ * mclahe_forward on the float32 volume of the same values; a given global
+ * range is in those units.  The output is float32 in [0, 1].
+ *   dtype     MCLAHE_F32 (same as mclahe_forward), MCLAHE_U16 or MCLAHE_U8.
+ *   d_in      device, prod(shape) elements of dtype, 16-byte aligned.
+ *   others    as for mclahe_forward.
+ * Integer volumes take the cluster form of the histogram pass (or the staged
+ * walk) and the per-thread mapping walks, whatever the plan's shapes.
+ * mclahe_backward and mclahe_batch take float32 volumes only.
+ * Returns as mclahe_forward, and MCLAHE_ERR_INVALID_ARG for an unknown dtype.
+ */
+MCLAHE_API mclahe_status mclahe_forward_typed(mclahe_plan_t plan, mclahe_dtype dtype, const void *d_in,
+                                              float *d_out, void *d_ws, size_t ws_bytes,
+                                              const float *d_clip, mclahe_stream_t stream);
+
 /* The passes of mclahe_forward, in the order it runs them. */
 typedef enum {
     MCLAHE_PASS_CLEAR = 0,  /* zero what later passes accumulate with atomics (memset): the
@@ -366,6 +394,71 @@ MCLAHE_API mclahe_status mclahe_forward_noalloc(mclahe_plan_t plan, const float 
  * nothing.  Returns MCLAHE_OK, the error device code recorded, or
  * MCLAHE_ERR_CUDA if the lookup or the copy fails. */
 MCLAHE_API mclahe_status mclahe_noalloc_sync_status(mclahe_stream_t stream);
+
+/*
+ * mclahe_metrics -- the contrast metrics the paper reports for its results
+ * (Sec. II; Tables I and II of Sec. IV), on the device.  The paper does not
+ * print their formulas; this library's readings:
+ *   every volume is normalised to [0, 1] by its own min and max (a constant
+ *   volume becomes 0);
+ *   d_out[0] = mean, d_out[1] = standard deviation (population, 1/n) of x;
+ *   d_out[2] = Shannon entropy in bits of x's 256-bin grey-level histogram
+ *              over its own [min, max] (bins by the fp32 quantiser of the
+ *              histogram pass);
+ *   d_out[3] = MSE = mean((x^ - ref^)^2), d_out[4] = PSNR = 10 log10(peak^2 /
+ *              MSE) dB with peak = 2^23, the peak that every (MSE, PSNR) pair
+ *              of Tables I-II implies (NaN for both when d_ref is NULL).
+ *   d_x, d_ref  device float32 volumes of n elements (d_ref nullable), 16-byte
+ *               aligned, distinct.
+ *   d_ws        device workspace of ws_bytes >= mclahe_metrics_workspace_bytes(n),
+ *               256-byte aligned (cleared by the call).
+ *   d_out       device double[5], 8-byte aligned.
+ * Sums are compensated fp32 per thread and fp64 across threads in a fixed
+ * order, so the result depends only on the inputs.  Does not synchronise.
+ * Returns MCLAHE_OK, MCLAHE_ERR_INVALID_ARG, MCLAHE_ERR_WORKSPACE, MCLAHE_ERR_CUDA.
+ */
+MCLAHE_API mclahe_status mclahe_metrics(const float *d_x, const float *d_ref, int64_t n, void *d_ws,
+                                        size_t ws_bytes, double *d_out, mclahe_stream_t stream);
+
+/* Workspace bytes of mclahe_metrics for n elements (0 for n < 1). */
+MCLAHE_API size_t mclahe_metrics_workspace_bytes(int64_t n);
+
+/*
+ * Pre-filters the paper applies before MCLAHE: a Gaussian (Sec. IV.A, the
+ * photoemission data, standard deviations 0.7, 0.9 and 1.3 along momenta,
+ * energy and time) and a median filter (Sec. IV.B, the fluorescence data,
+ * window (2, 2, 2, 1)).  The paper leaves boundary, truncation and the median
+ * of an even window open; readings (scipy.ndimage's conventions): the
+ * edge-inclusive mirror boundary of MCLAHE's padding (Sec. III.B), reflected
+ * as often as needed; Gaussian radius r = floor(4 sigma + 0.5).
+ * Volumes: device float32, C order, 1 <= ndim <= 4, every extent >= 1.
+ *
+ * mclahe_gaussian_weights -- host only (no CUDA call): the 2r + 1 fp32 weights
+ * of one dimension, exp(-k^2 / (2 sigma^2)) for k = -r..r normalised in double
+ * and rounded to fp32, into w[capacity]; *radius = r.  MCLAHE_ERR_UNSUPPORTED
+ * for r > 64.
+ *
+ * mclahe_filter_gaussian -- separable Gaussian of d_in into d_out, dimension 0
+ * first; sigma[ndim] >= 0 (0 leaves a dimension as it is).  Each output is the
+ * fp32 sum over the taps k = -r..r, in that order, of fp32(w_k * x) with every
+ * product and sum rounded to nearest, so the result is one exact function of
+ * the input.  d_tmp (device, n floats) is needed when two or more dimensions
+ * are filtered; no buffer may alias another.
+ *
+ * mclahe_filter_median -- median filter of d_in into d_out: window
+ * [x - floor(k/2), x - floor(k/2) + k - 1] along each dimension (size[ndim],
+ * at most 32 voxels in all), the value of rank floor(n/2) (0-based) of the
+ * window's n values (the upper median when n is even).
+ *
+ * None synchronises; argument errors return MCLAHE_ERR_INVALID_ARG without
+ * touching the device, a failed launch MCLAHE_ERR_CUDA.
+ */
+MCLAHE_API mclahe_status mclahe_gaussian_weights(float sigma, float *w, int capacity, int *radius);
+MCLAHE_API mclahe_status mclahe_filter_gaussian(const float *d_in, float *d_out, float *d_tmp, int ndim,
+                                                const int64_t *shape, const float *sigma,
+                                                mclahe_stream_t stream);
+MCLAHE_API mclahe_status mclahe_filter_median(const float *d_in, float *d_out, int ndim, const int64_t *shape,
+                                              const int32_t *size, mclahe_stream_t stream);
 
 /* Synchronise `stream`, then read and clear the device status word of the
  * workspace.  Returns MCLAHE_OK or the error device code recorded. */

@@ -34,8 +34,12 @@ EXPORTS = (
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
     "mclahe_plan_set_shapes", "mclahe_forward_graph", "mclahe_noalloc_sync_status",
-    "mclahe_batch_set_wait",
+    "mclahe_batch_set_wait", "mclahe_forward_typed", "mclahe_metrics",
+    "mclahe_metrics_workspace_bytes", "mclahe_gaussian_weights", "mclahe_filter_gaussian",
+    "mclahe_filter_median",
 )
+
+MCLAHE_F32, MCLAHE_U16, MCLAHE_U8 = 0, 1, 2
 
 MCLAHE_NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -127,6 +131,20 @@ def load(path: str = LIB_PATH):
         lib.mclahe_pass_launches.restype = ctypes.c_int
         lib.mclahe_forward_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.mclahe_forward_noalloc.restype = ctypes.c_int
+        lib.mclahe_gaussian_weights.argtypes = [f32, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.mclahe_gaussian_weights.restype = ctypes.c_int
+        lib.mclahe_filter_gaussian.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(f32), vp]
+        lib.mclahe_filter_gaussian.restype = ctypes.c_int
+        lib.mclahe_filter_median.argtypes = [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(i32), vp]
+        lib.mclahe_filter_median.restype = ctypes.c_int
+        lib.mclahe_metrics.argtypes = [vp, vp, ctypes.c_int64, vp, sz, vp, vp]
+        lib.mclahe_metrics.restype = ctypes.c_int
+        lib.mclahe_metrics_workspace_bytes.argtypes = [ctypes.c_int64]
+        lib.mclahe_metrics_workspace_bytes.restype = sz
+        lib.mclahe_forward_typed.argtypes = [vp, ctypes.c_int, vp, vp, vp, sz, vp, vp]
+        lib.mclahe_forward_typed.restype = ctypes.c_int
         lib.mclahe_noalloc_sync_status.argtypes = [vp]
         lib.mclahe_noalloc_sync_status.restype = ctypes.c_int
         lib.mclahe_batch_set_wait.argtypes = [ctypes.c_uint32, ctypes.c_int]
@@ -238,6 +256,54 @@ def mclahe_forward_graph(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=
     st = load().mclahe_forward_graph(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_ws), int(ws_bytes),
                                      _ptr(d_clip), _stream(stream))
     _check(st, "mclahe_forward_graph")
+
+
+def dtype_code(t) -> int:
+    """mclahe_dtype of a torch tensor (float32, uint16 or uint8)."""
+    import torch
+
+    codes = {torch.float32: MCLAHE_F32, torch.uint8: MCLAHE_U8}
+    if hasattr(torch, "uint16"):
+        codes[torch.uint16] = MCLAHE_U16
+    if t.dtype not in codes:
+        raise MclaheError(MCLAHE_ERR_INVALID_ARG, f"unsupported input dtype {t.dtype}")
+    return codes[t.dtype]
+
+
+def mclahe_forward_typed(plan, dtype, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
+    """Forward pass of a float32, uint16 or uint8 volume (dtype: MCLAHE_F32/U16/U8)."""
+    st = load().mclahe_forward_typed(plan.handle, int(dtype), _ptr(d_in), _ptr(d_out), _ptr(d_ws),
+                                     int(ws_bytes), _ptr(d_clip), _stream(stream))
+    _check(st, "mclahe_forward_typed")
+
+
+def mclahe_metrics_workspace_bytes(n) -> int:
+    return int(load().mclahe_metrics_workspace_bytes(int(n)))
+
+
+def mclahe_metrics(d_x, d_ref, n, d_ws, ws_bytes, d_out, stream=None):
+    """Contrast metrics of x (and MSE/PSNR against ref) into device double[5]."""
+    st = load().mclahe_metrics(_ptr(d_x), _ptr(d_ref), int(n), _ptr(d_ws), int(ws_bytes), _ptr(d_out),
+                               _stream(stream))
+    _check(st, "mclahe_metrics")
+
+
+def mclahe_filter_gaussian(d_in, d_out, d_tmp, shape, sigma, stream=None):
+    """Separable Gaussian pre-filter (device float32 volumes)."""
+    d = len(shape)
+    sh = (ctypes.c_int64 * d)(*[int(v) for v in shape])
+    sg = (ctypes.c_float * d)(*[float(v) for v in sigma])
+    _check(load().mclahe_filter_gaussian(_ptr(d_in), _ptr(d_out), _ptr(d_tmp), d, sh, sg, _stream(stream)),
+           "mclahe_filter_gaussian")
+
+
+def mclahe_filter_median(d_in, d_out, shape, size, stream=None):
+    """Median pre-filter (device float32 volumes)."""
+    d = len(shape)
+    sh = (ctypes.c_int64 * d)(*[int(v) for v in shape])
+    sz = (ctypes.c_int32 * d)(*[int(v) for v in size])
+    _check(load().mclahe_filter_median(_ptr(d_in), _ptr(d_out), d, sh, sz, _stream(stream)),
+           "mclahe_filter_median")
 
 
 def mclahe_forward_noalloc(plan, d_in, d_out, d_clip=None, stream=None):

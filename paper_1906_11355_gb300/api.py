@@ -39,20 +39,29 @@ class MCLAHE:
     def n_kernels(self):
         return int(self.info["n_kernels"])
 
-    def _check_volume(self, x):
-        if x.device.type != "cuda" or x.dtype != torch.float32 or not x.is_contiguous():
-            raise ValueError("expected a contiguous float32 CUDA tensor")
+    def _check_volume(self, x, integers=False):
+        ok = (torch.float32,) + ((torch.uint8,) + ((torch.uint16,) if hasattr(torch, "uint16") else ())
+                                 if integers else ())
+        if x.device.type != "cuda" or x.dtype not in ok or not x.is_contiguous():
+            raise ValueError("expected a contiguous " + ("float32, uint16 or uint8" if integers else "float32")
+                             + " CUDA tensor")
         if tuple(x.shape) != self.shape:
             raise ValueError(f"expected shape {self.shape}, got {tuple(x.shape)}")
 
     def forward(self, x, out=None, clip=None, stream=None, graph=False):
-        """Run Algorithm 1 on x; returns out (allocated if not given).
+        """Run Algorithm 1 on x; returns out (float32, allocated if not given).
 
+        x: float32, or uint16 / uint8 (intensities are the integers; mclahe_forward_typed).
         clip: optional 1-element float32 CUDA tensor overriding the clip limit.
-        graph: replay a CUDA graph cached per (x, out, clip) (mclahe_forward_graph)."""
-        self._check_volume(x)
+        graph: replay a CUDA graph cached per (x, out, clip) (mclahe_forward_graph;
+        float32 volumes)."""
+        self._check_volume(x, integers=True)
         if out is None:
-            out = torch.empty_like(x)
+            out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+        if x.dtype != torch.float32:
+            nat.mclahe_forward_typed(self.plan, nat.dtype_code(x), x, out, self.ws, self.ws_bytes, clip,
+                                     stream)
+            return out
         fwd = nat.mclahe_forward_graph if graph else nat.mclahe_forward
         fwd(self.plan, x, out, self.ws, self.ws_bytes, clip, stream)
         return out
@@ -153,3 +162,71 @@ class MCLAHEBatch:
         return outs
 
     __call__ = forward
+
+
+METRIC_NAMES = ("mean", "std", "entropy", "mse", "psnr")
+
+
+def contrast_metrics(x, ref=None, stream=None):
+    """Contrast metrics of a float32 CUDA volume (mclahe_metrics): mean, std,
+    entropy (bits, 256 grey levels) of x normalised to [0, 1], and with ref
+    the MSE and PSNR (peak 2^23) of x against ref, each normalised the same
+    way.  Returns a dict of floats (synchronises)."""
+    if x.dtype != torch.float32 or not x.is_contiguous() or x.device.type != "cuda":
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if ref is not None and (ref.shape != x.shape or ref.dtype != torch.float32 or not ref.is_contiguous()):
+        raise ValueError("ref must be a contiguous float32 tensor of x's shape")
+    n = x.numel()
+    ws = torch.empty(nat.mclahe_metrics_workspace_bytes(n), dtype=torch.uint8, device=x.device)
+    out = torch.empty(5, dtype=torch.float64, device=x.device)
+    nat.mclahe_metrics(x, ref, n, ws, ws.numel(), out, stream)
+    vals = out.cpu().tolist()
+    res = dict(zip(METRIC_NAMES, vals))
+    if ref is None:
+        del res["mse"], res["psnr"]
+    return res
+
+
+def compare_frames_vs_volume(x, kernel_size, n_bins=256, clip_limit=0.02, adaptive=False, use_graph=True):
+    """The paper's comparison (Sec. IV): D-dimensional CLAHE of the whole volume
+    against (D-1)-dimensional CLAHE of every frame along dimension 0, with
+    kernel_size[1:] for the frames (the same kernel in the frame dimensions).
+    x: contiguous float32 CUDA tensor, frames along dim 0 (contiguous views; the
+    frames run as one mclahe_batch call).  Returns (out_volume, out_frames,
+    metrics) where metrics holds contrast_metrics of both results against x."""
+    if x.dim() < 3:
+        raise ValueError("need at least 3 dimensions (frames along dimension 0)")
+    ks = tuple(int(b) for b in kernel_size)
+    vol = MCLAHE(x.shape, ks, n_bins, clip_limit, adaptive, device=x.device)
+    out_v = vol.forward(x)
+    spec = dict(shape=tuple(x.shape[1:]), kernel=ks[1:], n_bins=n_bins, clip_limit=clip_limit,
+                adaptive=adaptive)
+    frames = MCLAHEBatch([spec] * int(x.shape[0]), device=x.device)
+    out_f = torch.empty_like(x)
+    frames.forward([x[t] for t in range(x.shape[0])], outs=[out_f[t] for t in range(x.shape[0])],
+                   use_graph=use_graph)
+    return out_v, out_f, {"volume": contrast_metrics(out_v, x), "frames": contrast_metrics(out_f, x),
+                          "input": contrast_metrics(x)}
+
+
+def gaussian_filter(x, sigma, out=None, stream=None):
+    """Separable Gaussian pre-filter of a float32 CUDA volume (mclahe_filter_gaussian;
+    one sigma per dimension, mirror boundary, radius floor(4 sigma + 0.5))."""
+    if x.dtype != torch.float32 or not x.is_contiguous() or x.device.type != "cuda":
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if len(sigma) != x.dim():
+        raise ValueError("one sigma per dimension")
+    out = torch.empty_like(x) if out is None else out
+    tmp = torch.empty_like(x) if sum(1 for s in sigma if s > 0) >= 2 else None
+    nat.mclahe_filter_gaussian(x, out, tmp, tuple(x.shape), sigma, stream)
+    return out
+
+
+def median_filter(x, size, out=None, stream=None):
+    """Median pre-filter of a float32 CUDA volume (mclahe_filter_median; window
+    [x - k//2, x - k//2 + k - 1] per dimension, mirror boundary, upper median)."""
+    if x.dtype != torch.float32 or not x.is_contiguous() or x.device.type != "cuda":
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    out = torch.empty_like(x) if out is None else out
+    nat.mclahe_filter_median(x, out, tuple(x.shape), size, stream)
+    return out

@@ -6,7 +6,9 @@
 // row ring at most 200 KiB) x form: a cluster of C in {1, 2, 4, 8} CTAs per
 // item, or the flat form with S in {1, 2, 4, ..., 256} shares per item (with
 // its range pass, under the adaptive range) x row walk: the cp.async ring or
-// TMA tiles (where the geometry allows).  Mapping pass: per-thread loads
+// TMA tiles (where the geometry allows); and the staged walk (one kernel per
+// cluster of C in {1, 2, 4, 8} CTAs, its footprint in shared memory, where it
+// fits).  Mapping pass: per-thread loads
 // or TMA tiles (where the geometry allows) x CTAs per cell in {1, 2, 4, ...,
 // 64} (at most one row per CTA).  Each candidate runs twice
 // after one warm-up and keeps its faster time; results are cached per
@@ -123,6 +125,10 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
                         cands.push_back({G, R, th, walk, 1, S});
                 }
             }
+    // the staged walk: one kernel per cluster of 1..8 CTAs
+    for (int R = 2; R <= 32; R <<= 1)
+        for (int C = 1; C <= 8; C <<= 1)
+            if (hist_staged_fits(p->g, R, C, nullptr)) cands.push_back({1, R, 256, 3, C, 0});
     for (const Cand &c : cands) {
         if (s != MCLAHE_OK) break;
         p->t.hist_group = c.G;

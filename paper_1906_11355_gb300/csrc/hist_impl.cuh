@@ -221,23 +221,38 @@ __device__ __forceinline__ void block_lut(const uint32_t *h, int nb, int LS, int
     for (int j = nb + int(threadIdx.x); j < LS; j += blockDim.x) out[j] = st.flat ? 0.0f : 1.0f;
 }
 
-// The same table built by one warp (lane l owns bins l, l + 32, ...; a warp
-// scan per 32 bins carries the prefixes), so the warps of a block build
-// several kernels' tables at once.  The statistics are the same integers and
-// the same float operations as block_lut's: the tables are identical.
+// The same table built by one warp, so the warps of a block build several
+// kernels' tables at once.  Lane l owns the contiguous bins [l c, l c + c),
+// c = ceil(nb / 32): one pass over its bins for the unclipped sum and clipped
+// count, one warp scan for the prefixes at its first bin, then its bins in
+// order.  The statistics are the same integers and every entry the same float
+// operations as block_lut's: the tables are identical.
 __device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int64_t V, float clip,
                                          float *__restrict__ out) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     LutStats st;
     clip_threshold(clip, V, st.tf, st.tr);
+    const int per = (nb + 31) >> 5;
+    const int j0 = min(lane * per, nb), j1 = min(j0 + per, nb);
     uint32_t nc = 0, su = 0;
-    for (int j = lane; j < nb; j += 32) {
+    for (int j = j0; j < j1; ++j) {
         const uint32_t v = h[j];
         if (int64_t(v) > st.tf) nc += 1; else su += v;
     }
-    st.S_tot = __reduce_add_sync(full, su);
-    st.N_c = __reduce_add_sync(full, nc);
+    // inclusive warp scans of the per-lane sums
+    uint32_t is = su, ia = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t xs = __shfl_up_sync(full, is, o);
+        const uint32_t xa = __shfl_up_sync(full, ia, o);
+        if (lane >= o) {
+            is += xs;
+            ia += xa;
+        }
+    }
+    st.S_tot = __shfl_sync(full, is, 31);
+    st.N_c = __shfl_sync(full, ia, 31);
     const uint32_t v0 = h[0];
     st.S0 = (int64_t(v0) > st.tf) ? 0 : v0;
     st.A0 = (int64_t(v0) > st.tf) ? 1 : 0;
@@ -246,24 +261,11 @@ __device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int6
     st.Eb = __fdiv_rn(E, float(nb));
     st.flat = (st.N_c == 0) && (st.S_tot == st.S0);
     st.den = st.diff(st.S_tot, st.N_c, nb - 1);
-    int64_t cs = 0, ca = 0;   // S and A over the earlier chunks
-    for (int j0 = 0; j0 < nb; j0 += 32) {
-        const int j = j0 + lane;
-        const uint32_t v = j < nb ? h[j] : 0u;
-        const bool over = j < nb && int64_t(v) > st.tf;
-        uint32_t s = over ? 0u : v, a = over ? 1u : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t xs = __shfl_up_sync(full, s, o);
-            const uint32_t xa = __shfl_up_sync(full, a, o);
-            if (lane >= o) {
-                s += xs;
-                a += xa;
-            }
-        }
-        if (j < nb) out[j] = st.flat ? 0.0f : __fdiv_rn(st.diff(cs + s, ca + a, j), st.den);
-        cs += __shfl_sync(full, s, 31);
-        ca += __shfl_sync(full, a, 31);
+    int64_t Sj = is - su, Aj = ia - nc;   // exclusive prefixes at j0
+    for (int j = j0; j < j1; ++j) {
+        const uint32_t v = h[j];
+        if (int64_t(v) > st.tf) Aj += 1; else Sj += v;
+        out[j] = st.flat ? 0.0f : __fdiv_rn(st.diff(Sj, Aj, j), st.den);
     }
     for (int j = nb + lane; j < LS; j += 32) out[j] = st.flat ? 0.0f : 1.0f;
 }
@@ -367,6 +369,64 @@ __device__ __forceinline__ Targets last_targets(const Dim &d, int x, int kl0, in
     return t;
 }
 
+// Phase 4 of the cluster form: cluster rank r owns kernels r, r + C, ... of
+// the GK kernels of the item: it sums the CTAs' counts (cnt, [GK][P] in every
+// CTA's shared memory) in rank order into its own copy area (sh, free now),
+// stores the histograms and ranges and builds the mapping tables.  Every CTA
+// of the cluster calls it after a cluster barrier that follows the counts.
+__device__ __forceinline__ void merge_and_build(const Geom &g, uint32_t *sh, uint32_t *cnt,
+                                                const float *s_lo, const float *s_sc, int GK, int C,
+                                                int rank, uint32_t *__restrict__ hist,
+                                                float *__restrict__ lut, float *__restrict__ lo_out,
+                                                float *__restrict__ scale_out, int64_t kfirst,
+                                                const float *__restrict__ d_clip) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int nb = g.nb, P = g.P;
+    const int n_own = GK > rank ? (GK - rank + C - 1) / C : 0;
+    uint32_t *own = sh;   // [n_own][P]
+    for (int t = threadIdx.x; t < n_own * nb; t += blockDim.x) {
+        const int i = t / nb, j = t - i * nb;
+        const int kg = rank + i * C;
+        uint32_t s = 0;
+        if (C > 1) {
+            for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
+        } else {
+            s = cnt[size_t(kg) * P + j];
+        }
+        own[size_t(i) * P + j] = s;
+        hist[(kfirst + kg) * nb + j] = s;
+    }
+    for (int i = threadIdx.x; i < n_own; i += blockDim.x) {
+        const int kg = rank + i * C;
+        lo_out[kfirst + kg] = s_lo[kg];
+        scale_out[kfirst + kg] = s_sc[kg];
+    }
+    __syncthreads();
+    if (n_own > 0)
+        build_luts(own, P, n_own, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut, kfirst + rank, C);
+    if (C > 1) cluster.sync(); else __syncthreads();   // the other CTAs' shared memory is no longer read
+}
+
+// Phase 3: sum the R lane copies of every bin of GK kernels (copy (c + j) mod
+// R of bin j at step c: the threads of a warp read different banks) into
+// cnt[GK][P] and fold the padded indices >= n_bins - 1 into the last bin.
+// All threads of the block call it after the sweep's barrier.
+__device__ __forceinline__ void sum_copies(const uint32_t *sh, uint32_t *cnt, int GK, int P, int R,
+                                           int nb) {
+    for (int t = threadIdx.x; t < GK * P; t += blockDim.x) {
+        const int j = t % P;
+        const uint32_t *row = sh + size_t(t) * R;
+        uint32_t s = 0;
+        for (int c = 0; c < R; ++c) s += row[(c + j) & (R - 1)];
+        cnt[t] = s;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < GK * (P - nb); t += blockDim.x) {
+        const int kg = t / (P - nb), j = nb + t % (P - nb);
+        atomicAdd(&cnt[kg * P + nb - 1], cnt[kg * P + j]);
+    }
+}
+
 // Modes of hist_group:
 //   kHistCluster   one thread-block cluster per item (phases 1-4 below; the
 //                  ranks split the rows, merge through DSMEM, build the tables);
@@ -381,8 +441,8 @@ __device__ __forceinline__ Targets last_targets(const Dim &d, int x, int kl0, in
 //                  per-kernel keys with atomic max.
 constexpr int kHistCluster = 0, kHistFlat = 1, kHistMinMax = 2;
 
-template <int D, bool ADAPTIVE, int MODE = kHistCluster, int HW = kHistLsu>
-__device__ __forceinline__ void hist_group(const Geom &g, const float *__restrict__ in,
+template <int D, bool ADAPTIVE, int MODE = kHistCluster, int HW = kHistLsu, typename T = float>
+__device__ __forceinline__ void hist_group(const Geom &g, const T *__restrict__ in,
                                            const uint32_t *__restrict__ keys,
                                            const float *__restrict__ d_clip,
                                            uint32_t *__restrict__ hist, float *__restrict__ lut,
@@ -522,7 +582,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                 rest = small_div(rest, len[j], rr);
                 a += int64_t(box_lo[j] + rr) * stride[j];
             }
-            fn(box_lo[D - 1] + e, __ldg(in + a));
+            fn(box_lo[D - 1] + e, ld1(in + a));
         }
     };
 
@@ -726,13 +786,32 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     }
     __syncthreads();
 
-    // ---- phase 2: histogram sweep
+    // ---- phase 2: histogram sweep.  Copies: the lanes of a warp that read the
+    // same quad position of different rows (and so may add to the same kernel)
+    // take different copies: with LPR lanes per row, lane = r * LPR + gl adds
+    // to copy (r + gl * 32 / LPR) mod R.  With ZC the voxels in bin 0 are
+    // counted in a register per quad slot and added once per box (measured
+    // slower on count data than one reduction per voxel: off).
     {
+        constexpr bool ZC = false;
         const uint32_t sh_base = uint32_t(__cvta_generic_to_shared(sh));
         const uint32_t r4 = uint32_t(4 * R);
         const uint32_t lane_off = 4u * uint32_t(lane & (R - 1));
         const uint32_t kstride = uint32_t(P) * r4;   // bytes per kernel's copies
         const float iqk = g.iqk, qkf = g.qkf;
+        // copy offset of this lane when LPR lanes share a row (LPR a power of
+        // two <= 32; 0: lane order)
+        auto copy_off = [&](int lpr) {
+            if (lpr <= 1 || lpr > 32 || (lpr & (lpr - 1))) return lane_off;
+            return 4u * uint32_t(((lane / lpr) + (lane % lpr) * (32 / lpr)) & (R - 1));
+        };
+        // lanes per row of the walk a box takes
+        auto box_lpr = [&](const int *box_lo, const int *len, const TileShape &ts) {
+            if constexpr (HW == kHistTma) {
+                if ((box_lo[D - 1] & 3) + len[D - 1] <= htma->bx) return htma->bx / 4;
+            }
+            return ts.LPR;
+        };
         auto add_elem = [&](int x, float v, uint32_t w) {
             const Targets tg = last_targets(dl, x, kl0, kl1);
 #pragma unroll
@@ -744,6 +823,16 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                                    w * uint32_t(tg.m[t]));
                 }
         };
+        // one voxel of a whole quad: bin 0 counted in z (ZC), else reduced
+        auto add_bits = [&](uint32_t bits, uint32_t base, uint32_t w, uint32_t &z) {
+            if (ZC) {
+                if (bits == kBinBias) {
+                    z += 1u;
+                    return;
+                }
+            }
+            red_shared_add(bits * r4 + base, w);
+        };
         for_boxes([&](const int *box_lo, const int *len, int w, int r0, int r1, int kgfix) {
             const int L = len[D - 1], xs = box_lo[D - 1];
             const uint32_t wu = uint32_t(w);
@@ -754,18 +843,20 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                     int q0;          // element offset of the slot in the row
                     bool full;       // all four voxels inside the box
                 };
-                const uint32_t base = sh_base + uint32_t(kgfix) * kstride + lane_off - kBinBias * r4;
+                const uint32_t base = sh_base + uint32_t(kgfix) * kstride +
+                                      copy_off(box_lpr(box_lo, len, ts)) - kBinBias * r4;
                 const float2 n2 = make_float2(s_nlo[kgfix], s_nlo[kgfix]);
                 const float2 s2 = make_float2(s_sc[kgfix], s_sc[kgfix]);
+                uint32_t z = 0;
                 auto slot = [&](int, int e0) { return FSlot{e0, e0 >= 0 && e0 + 4 <= L}; };
                 auto quad = [&](NoRow &, const FSlot &sd, int, const float4 &v, const float4 &, int64_t) {
                     const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
                     const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
                     if (sd.full) {
-                        red_shared_add(b01.x * r4 + base, wu);
-                        red_shared_add(b01.y * r4 + base, wu);
-                        red_shared_add(b23.x * r4 + base, wu);
-                        red_shared_add(b23.y * r4 + base, wu);
+                        add_bits(b01.x, base, wu, z);
+                        add_bits(b01.y, base, wu, z);
+                        add_bits(b23.x, base, wu, z);
+                        add_bits(b23.y, base, wu, z);
                     } else {
                         const uint32_t bits[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
@@ -778,39 +869,55 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                                          int64_t) {
                         const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
                         const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
-                        red_shared_add(b01.x * r4 + base, wu);
-                        red_shared_add(b01.y * r4 + base, wu);
-                        red_shared_add(b23.x * r4 + base, wu);
-                        red_shared_add(b23.y * r4 + base, wu);
+                        add_bits(b01.x, base, wu, z);
+                        add_bits(b01.y, base, wu, z);
+                        add_bits(b23.x, base, wu, z);
+                        add_bits(b23.y, base, wu, z);
                     };
                     walk_full(Tag<FSlot>{}, box_lo, len, r0, r1, ts, slot, quad_full);
                 } else {
                     walk(Tag<FSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
                 }
+                if (ZC && z) red_shared_add(kBinBias * r4 + base, z * wu);
             } else if (tiled) {
                 // groups of kernels: a slot's quad goes to one kernel (with
                 // one multiplicity) when its first and last voxel do -- the
                 // targets change monotonically along x -- else voxel by voxel
                 const TileShape ts = tile_shape(L, xs & 3, blockDim.x, kHistQmax);
+                const uint32_t coff = copy_off(box_lpr(box_lo, len, ts));
                 struct HSlot {
                     uint32_t base;   // copy address of bin 0 minus the bias; ~0: per-voxel path
                     uint32_t w;      // weight of the slot's voxels
                     int q0;          // element offset of the slot in the row
                     int kg;          // the slot's kernel (adaptive range constants)
                 };
-                auto slot = [&](int, int e0) {
+                // bin-0 counts per slot (ZC), with the slot's address and weight
+                uint32_t zc[kHistQmax], zbase[kHistQmax], zw[kHistQmax];
+#pragma unroll
+                for (int i = 0; i < kHistQmax; ++i) {
+                    zc[i] = 0;
+                    zbase[i] = 0xffffffffu;
+                    zw[i] = 0;
+                }
+                auto slot = [&](int i, int e0) {
                     HSlot sd{0xffffffffu, 0u, e0, 0};
                     if (e0 < 0 || e0 + 4 > L) return sd;
                     const Targets t0 = last_targets(dl, xs + e0, kl0, kl1);
                     const Targets t1 = last_targets(dl, xs + e0 + 3, kl0, kl1);
                     if (t0.n != 1 || t1.n != 1 || t1.kg[0] != t0.kg[0] || t1.m[0] != t0.m[0]) return sd;
-                    sd.base = sh_base + uint32_t(t0.kg[0]) * kstride + lane_off - kBinBias * r4;
+                    sd.base = sh_base + uint32_t(t0.kg[0]) * kstride + coff - kBinBias * r4;
                     sd.w = wu * uint32_t(t0.m[0]);
                     sd.kg = t0.kg[0];
+#pragma unroll
+                    for (int j = 0; j < kHistQmax; ++j)
+                        if (j == i) {
+                            zbase[j] = sd.base;
+                            zw[j] = sd.w;
+                        }
                     return sd;
                 };
                 const float2 gnl = make_float2(s_nlo[0], s_nlo[0]), gsc = make_float2(s_sc[0], s_sc[0]);
-                auto quad = [&](NoRow &, const HSlot &sd, int, const float4 &v, const float4 &, int64_t) {
+                auto quad = [&](NoRow &, const HSlot &sd, int i, const float4 &v, const float4 &, int64_t) {
                     if (sd.base != 0xffffffffu) {
                         float2 n2 = gnl, s2 = gsc;
                         if (ADAPTIVE) {
@@ -819,10 +926,16 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                         }
                         const uint2 b01 = qbits2(make_float2(v.x, v.y), n2, s2, iqk, qkf);
                         const uint2 b23 = qbits2(make_float2(v.z, v.w), n2, s2, iqk, qkf);
-                        red_shared_add(b01.x * r4 + sd.base, sd.w);
-                        red_shared_add(b01.y * r4 + sd.base, sd.w);
-                        red_shared_add(b23.x * r4 + sd.base, sd.w);
-                        red_shared_add(b23.y * r4 + sd.base, sd.w);
+                        uint32_t z = 0;
+                        add_bits(b01.x, sd.base, sd.w, z);
+                        add_bits(b01.y, sd.base, sd.w, z);
+                        add_bits(b23.x, sd.base, sd.w, z);
+                        add_bits(b23.y, sd.base, sd.w, z);
+                        if (ZC) {
+#pragma unroll
+                            for (int j = 0; j < kHistQmax; ++j)
+                                if (j == i) zc[j] += z;
+                        }
                     } else {
                         const float vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -831,6 +944,11 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
                     }
                 };
                 walk(Tag<HSlot>{}, box_lo, len, r0, r1, ts, slot, quad);
+                if (ZC) {
+#pragma unroll
+                    for (int i = 0; i < kHistQmax; ++i)
+                        if (zc[i]) red_shared_add(kBinBias * r4 + zbase[i], zc[i] * zw[i]);
+                }
             } else {
                 // rows at varying alignments: voxel by voxel
                 for_voxels(box_lo, len, r0, r1, [&](int x, float v) {
@@ -846,20 +964,8 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
     }
     __syncthreads();
 
-    // ---- phase 3: sum the copies (copy (c + j) mod R of bin j at step c: the
-    // threads of a warp read different banks), fold the padded indices
-    for (int t = threadIdx.x; t < GK * P; t += blockDim.x) {
-        const int j = t % P;
-        const uint32_t *row = sh + size_t(t) * R;
-        uint32_t s = 0;
-        for (int c = 0; c < R; ++c) s += row[(c + j) & (R - 1)];
-        cnt[t] = s;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < GK * (P - nb); t += blockDim.x) {
-        const int kg = t / (P - nb), j = nb + t % (P - nb);
-        atomicAdd(&cnt[kg * P + nb - 1], cnt[kg * P + j]);
-    }
+    // ---- phase 3: sum the copies, fold the padded indices
+    sum_copies(sh, cnt, GK, P, R, nb);
     if (MODE == kHistFlat) {
         __syncthreads();
         // add this CTA's counts to the item's global histograms
@@ -892,33 +998,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const float *__restric
         return;
     }
     csync();   // every CTA's counts are complete
-
-    // ---- phase 4: rank r owns kernels r, r + C, ...: sums the CTAs' counts
-    // in rank order into the copy area (free now), stores the histograms and
-    // ranges, builds the mapping tables
-    const int n_own = GK > rank ? (GK - rank + C - 1) / C : 0;
-    uint32_t *own = sh;   // [n_own][P]
-    for (int t = threadIdx.x; t < n_own * nb; t += blockDim.x) {
-        const int i = t / nb, j = t - i * nb;
-        const int kg = rank + i * C;
-        uint32_t s = 0;
-        if (C > 1) {
-            for (int c = 0; c < C; ++c) s += cluster.map_shared_rank(cnt, c)[size_t(kg) * P + j];
-        } else {
-            s = cnt[size_t(kg) * P + j];
-        }
-        own[size_t(i) * P + j] = s;
-        hist[(kfirst + kg) * nb + j] = s;
-    }
-    for (int i = threadIdx.x; i < n_own; i += blockDim.x) {
-        const int kg = rank + i * C;
-        lo_out[kfirst + kg] = s_lo[kg];
-        scale_out[kfirst + kg] = s_sc[kg];
-    }
-    __syncthreads();
-    if (n_own > 0)
-        build_luts(own, P, n_own, nb, g.LS, g.V, load_clip(d_clip, g.clip), lut, kfirst + rank, C);
-    csync();   // the other CTAs' shared memory is no longer read
+    merge_and_build(g, sh, cnt, s_lo, s_sc, GK, C, rank, hist, lut, lo_out, scale_out, kfirst, d_clip);
 }
 
 }  // namespace mclahe

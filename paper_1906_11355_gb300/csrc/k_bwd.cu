@@ -390,8 +390,10 @@ __global__ void __launch_bounds__(256) k_clipgrad(const float *__restrict__ dT, 
 }
 
 size_t bwd_sum_words(const Geom &g) { return size_t(n_cells(g)) * (size_t(1) << g.D) * size_t(g.LS); }
-size_t bwd_scratch_bytes(const Geom &g) {
-    return 8 * bwd_sum_words(g) + 16 + sizeof(float) * size_t(g.K);
+// the scatter's sums, max |g| key and dL/dT, or the gather's tables and
+// partials (k_bwd_gather.cu), whichever is larger: both start at the scratch
+size_t bwd_scratch_bytes(const Geom &g, int chunks) {
+    return std::max(8 * bwd_sum_words(g) + 16 + sizeof(float) * size_t(g.K), bwd_gather_bytes(g, chunks));
 }
 
 template <int D>
@@ -445,6 +447,8 @@ static cudaError_t launch_bwd_d(const mclahe_plan_s &p, const float *in, const f
 cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float *gout,
                             unsigned char *ws, const float *d_clip, float *d_grad_lut,
                             float *d_grad_clip, cudaStream_t st) {
+    // the clip-limit gradient alone: the gather form (no table gradients needed)
+    if (!d_grad_lut && d_grad_clip) return launch_backward_gather(p, in, gout, ws, d_clip, d_grad_clip, st);
     switch (p.g.D) {
         case 1: return launch_bwd_d<1>(p, in, gout, ws, d_clip, d_grad_lut, d_grad_clip, st);
         case 2: return launch_bwd_d<2>(p, in, gout, ws, d_clip, d_grad_lut, d_grad_clip, st);

@@ -65,6 +65,8 @@ cudaError_t launch_hist_tma(const mclahe_plan_s &p, const float *in, unsigned ch
                             const float *d_clip, cudaStream_t st, bool range, int bx, int by);
 cudaError_t launch_hist_lsu(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                             const float *d_clip, cudaStream_t st, bool range);
+cudaError_t launch_hist_staged(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+                               const float *d_clip, cudaStream_t st);
 
 static cudaError_t launch_any(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                               const float *d_clip, cudaStream_t st, bool range) {
@@ -72,6 +74,7 @@ static cudaError_t launch_any(const mclahe_plan_s &p, const float *in, unsigned 
     if (p.t.hist_walk == 1 && hist_tma_box(p.g, p.t.hist_group, bx, by))
         return launch_hist_tma(p, in, ws, d_clip, st, range, bx, by);
     if (p.t.hist_walk == 2) return launch_hist_lsu(p, in, ws, d_clip, st, range);
+    if (p.t.hist_walk == 3 && !range) return launch_hist_staged(p, in, ws, d_clip, st);
     HistTmaArgs none;
     std::memset(&none.map, 0, sizeof(none.map));
     return launch_hist_walk<kHistRing>(p, in, ws, d_clip, st, none, range);

@@ -14,6 +14,8 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "hist_impl.cuh"
 
@@ -27,10 +29,10 @@ __device__ __forceinline__ uint32_t hist_tma_stage0(const uint32_t *sh, size_t w
 
 // 4-D volumes also run 512-thread CTAs (their lane copies fill the shared
 // memory, so twice the warps per SM share one copy set).
-template <int D, bool ADAPTIVE, int HW>
+template <int D, bool ADAPTIVE, int HW, typename T = float>
 __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistTma ? 2 : 3))
     k_hist(Geom g, const __grid_constant__ CUtensorMap tmap, int tbx, int tby,
-           const float *__restrict__ in, const uint32_t *__restrict__ keys,
+           const T *__restrict__ in, const uint32_t *__restrict__ keys,
            const float *__restrict__ d_clip, uint32_t *__restrict__ hist, float *__restrict__ lut,
            float *__restrict__ lo_out, float *__restrict__ scale_out, int G, int R,
            uint32_t *status) {
@@ -42,16 +44,16 @@ __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistT
         tr = tma_ring_init<kHistTmaStages>(s_tbar, hist_tma_stage0(sh, hist_smem_words(g.P, R, G)),
                                            status);
     const HistTma ht{&tmap, tbx, tby};
-    hist_group<D, ADAPTIVE, kHistCluster, HW>(g, in, keys, d_clip, hist, lut, lo_out, scale_out,
+    hist_group<D, ADAPTIVE, kHistCluster, HW, T>(g, in, keys, d_clip, hist, lut, lo_out, scale_out,
                                               item, G, R, sh, 0, 1, 1, nullptr, nullptr, &ht, &tr);
 }
 
 // Flat forms: CTA b takes shares [total * b / grid, total * (b + 1) / grid)
 // of the work items' S shares each, item by item.
-template <int D, bool ADAPTIVE, int MODE, int HW>
+template <int D, bool ADAPTIVE, int MODE, int HW, typename T = float>
 __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistTma ? 2 : 3))
     k_hist_flat(Geom g, const __grid_constant__ CUtensorMap tmap, int tbx, int tby,
-                const float *__restrict__ in, const uint32_t *__restrict__ keys,
+                const T *__restrict__ in, const uint32_t *__restrict__ keys,
                 const float *__restrict__ d_clip, uint32_t *__restrict__ hist,
                 float *__restrict__ lut, float *__restrict__ lo_out, float *__restrict__ scale_out,
                 uint32_t *__restrict__ kkeys, uint32_t *__restrict__ tickets, int G, int R, int S,
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistT
         const int c0 = int(s - item * S);
         const int64_t rest = b1 - item * S;
         const int c1 = rest < S ? int(rest) : S;
-        hist_group<D, ADAPTIVE, MODE, HW>(g, in, keys, d_clip, hist, lut, lo_out, scale_out, item, G,
+        hist_group<D, ADAPTIVE, MODE, HW, T>(g, in, keys, d_clip, hist, lut, lo_out, scale_out, item, G,
                                           R, sh, c0, c1, S, tickets, kkeys, &ht, &tr);
         s = item * S + c1;
         __syncthreads();   // shared memory is reused by the next item
@@ -85,13 +87,13 @@ struct HistTmaArgs {
     int bx = 0, by = 0;
 };
 
-template <int D, bool ADAPTIVE, int HW>
-static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+template <int D, bool ADAPTIVE, int HW, typename T>
+static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const T *in, unsigned char *ws,
                                        const float *d_clip, cudaStream_t st, const HistTmaArgs &ta) {
     const Geom &g = p.g;
     const int C = p.t.hist_chunks;
     const size_t smem = hist_smem_bytes(g, p.t.hist_copies, p.t.hist_group, HW, p.t.hist_threads);
-    auto kern = k_hist<D, ADAPTIVE, HW>;
+    auto kern = k_hist<D, ADAPTIVE, HW, T>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), size_t(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -117,14 +119,14 @@ static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const float *in, 
 
 // One launch of a flat form: a persistent grid of as many CTAs as fit on the
 // device at once (at most one per share).
-template <int D, bool ADAPTIVE, int MODE, int HW>
-static cudaError_t launch_hist_flat(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+template <int D, bool ADAPTIVE, int MODE, int HW, typename T>
+static cudaError_t launch_hist_flat(const mclahe_plan_s &p, const T *in, unsigned char *ws,
                                     const float *d_clip, cudaStream_t st, const HistTmaArgs &ta) {
     const Geom &g = p.g;
     const int G = p.t.hist_group, R = p.t.hist_copies, S = p.t.hist_shares;
     const size_t smem = MODE == kHistMinMax ? hist_range_smem_bytes(G, HW, p.t.hist_threads)
                                             : hist_smem_bytes(g, R, G, HW, p.t.hist_threads);
-    auto kern = k_hist_flat<D, ADAPTIVE, MODE, HW>;
+    auto kern = k_hist_flat<D, ADAPTIVE, MODE, HW, T>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), size_t(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -147,20 +149,20 @@ static cudaError_t launch_hist_flat(const mclahe_plan_s &p, const float *in, uns
 
 // Histogram pass (or, with RANGE, the flat form's adaptive range pass) of a
 // D-dimensional volume with row walk HW.
-template <int HW>
-static cudaError_t launch_hist_walk(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+template <int HW, typename T = float>
+static cudaError_t launch_hist_walk(const mclahe_plan_s &p, const T *in, unsigned char *ws,
                                     const float *d_clip, cudaStream_t st, const HistTmaArgs &ta,
                                     bool range) {
     const bool adaptive = p.g.mode == MCLAHE_RANGE_ADAPTIVE;
     const bool flat = p.t.hist_shares > 0;
     auto go = [&](auto dtag) -> cudaError_t {
         constexpr int D = decltype(dtag)::value;
-        if (range) return launch_hist_flat<D, true, kHistMinMax, HW>(p, in, ws, nullptr, st, ta);
+        if (range) return launch_hist_flat<D, true, kHistMinMax, HW, T>(p, in, ws, nullptr, st, ta);
         if (flat)
-            return adaptive ? launch_hist_flat<D, true, kHistFlat, HW>(p, in, ws, d_clip, st, ta)
-                            : launch_hist_flat<D, false, kHistFlat, HW>(p, in, ws, d_clip, st, ta);
-        return adaptive ? launch_hist_cluster<D, true, HW>(p, in, ws, d_clip, st, ta)
-                        : launch_hist_cluster<D, false, HW>(p, in, ws, d_clip, st, ta);
+            return adaptive ? launch_hist_flat<D, true, kHistFlat, HW, T>(p, in, ws, d_clip, st, ta)
+                            : launch_hist_flat<D, false, kHistFlat, HW, T>(p, in, ws, d_clip, st, ta);
+        return adaptive ? launch_hist_cluster<D, true, HW, T>(p, in, ws, d_clip, st, ta)
+                        : launch_hist_cluster<D, false, HW, T>(p, in, ws, d_clip, st, ta);
     };
     switch (p.g.D) {
         case 2: return go(std::integral_constant<int, 2>{});

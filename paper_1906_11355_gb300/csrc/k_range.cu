@@ -36,17 +36,17 @@ __device__ __forceinline__ void block_minmax(float &mn, float &mx) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_range_global(const float *__restrict__ in, int64_t n,
+template <typename T>
+__global__ void __launch_bounds__(256) k_range_global(const T *__restrict__ in, int64_t n,
                                                       uint32_t *__restrict__ keys) {
     float mn = INFINITY, mx = -INFINITY;
     const int64_t nq = n >> 2;
-    const float4 *in4 = reinterpret_cast<const float4 *>(in);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     for (; i + 3 * stride < nq; i += 4 * stride) {   // four loads in flight
         float4 v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldcs(in4 + i + u * stride);
+        for (int u = 0; u < 4; ++u) v[u] = ldq(in + 4 * (i + u * stride), true);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             mn = fminf(mn, fminf(fminf(v[u].x, v[u].y), fminf(v[u].z, v[u].w)));
@@ -54,12 +54,12 @@ __global__ void __launch_bounds__(256) k_range_global(const float *__restrict__ 
         }
     }
     for (; i < nq; i += stride) {
-        float4 v = __ldcs(in4 + i);
+        const float4 v = ldq(in + 4 * i, true);
         mn = fminf(mn, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
         mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
     }
     for (int64_t t = (nq << 2) + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += stride) {
-        float v = in[t];
+        const float v = ld1(in + t);
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
     }
@@ -70,18 +70,32 @@ __global__ void __launch_bounds__(256) k_range_global(const float *__restrict__ 
     }
 }
 
-cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
-                         cudaStream_t st) {
+template <typename T>
+static cudaError_t launch_range_t(const mclahe_plan_s &p, const T *in, unsigned char *ws,
+                                  cudaStream_t st) {
     const Geom &g = p.g;
     uint32_t *keys = reinterpret_cast<uint32_t *>(ws + p.ws.keys);
     if (g.mode == MCLAHE_RANGE_GLOBAL) {
         if (g.has_range) return cudaSuccess;
         int64_t nq = (g.N >> 2) + 1;
-        int blocks = int(std::min<int64_t>((nq + 255) / 256, 152 * 4));
-        k_range_global<<<blocks, 256, 0, st>>>(in, g.N, keys);
+        int blocks = int(std::min<int64_t>((nq + 255) / 256, int64_t(device_sms()) * 4));
+        k_range_global<T><<<blocks, 256, 0, st>>>(in, g.N, keys);
         return cudaGetLastError();
     }
     return cudaSuccess;   // the adaptive range is fused into the histogram pass
+}
+
+cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+                         cudaStream_t st) {
+    return launch_range_t(p, in, ws, st);
+}
+cudaError_t launch_range_u16(const mclahe_plan_s &p, const uint16_t *in, unsigned char *ws,
+                             cudaStream_t st) {
+    return launch_range_t(p, in, ws, st);
+}
+cudaError_t launch_range_u8(const mclahe_plan_s &p, const uint8_t *in, unsigned char *ws,
+                            cudaStream_t st) {
+    return launch_range_t(p, in, ws, st);
 }
 
 }  // namespace mclahe

@@ -99,13 +99,20 @@ __host__ __device__ inline size_t map_smem_for(int D, int P, bool ring = true) {
 
 __device__ __forceinline__ void sts128(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-template <int D, bool ADAPTIVE, bool REPL, int WALK = kWalkRing>
-__device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict__ in,
+// DOT: instead of storing the mapped voxels, the CTA's threads accumulate
+// sum_v gout[v] * mapped(v) over their voxels (x and gout read together with
+// per-thread loads) into *dot as a compensated (Kahan) float pair (sum,
+// correction); the tables `lut` are then whatever per-kernel tables the caller
+// interpolates (the clip-limit gradient uses d lut / dT).
+template <int D, bool ADAPTIVE, bool REPL, int WALK = kWalkRing, bool DOT = false,
+          typename T = float>
+__device__ __forceinline__ void map_cell(const Geom &g, const T *__restrict__ in,
                                          float *__restrict__ out, const float *__restrict__ lut,
                                          const float *__restrict__ lo_k,
                                          const float *__restrict__ scale_k, int64_t cell, int chunk,
                                          int chunks, float *tab, const MapTma *tma = nullptr,
-                                         int chunk_end = -1) {
+                                         int chunk_end = -1, const float *__restrict__ gout = nullptr,
+                                         float2 *dot = nullptr) {
     // rows [R * chunk / chunks, R * chunk_end / chunks) of the cell (chunk_end
     // defaults to chunk + 1)
     if (chunk_end < 0) chunk_end = chunk + 1;
@@ -414,6 +421,61 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         }
     };
 
+    if constexpr (DOT) {
+        float ks = 0.0f, kc = 0.0f;   // Kahan sum of gout * mapped
+        auto kadd = [&](float t) {
+            const float y = __fsub_rn(t, kc);
+            const float s2 = __fadd_rn(ks, y);
+            kc = __fsub_rn(__fsub_rn(s2, ks), y);
+            ks = s2;
+        };
+        if ((g.d[D - 1].s & 3) == 0) {
+            constexpr int QM = 4;
+            struct DSlot {
+                float fbi;   // last-dim weight w1 of the slot's first voxel
+                int e0;
+            };
+            const TileShape ts = tile_shape(L, xl & 3, blockDim.x, QM);
+            auto slot = [&](int, int e0) {
+                DSlot sd;
+                sd.e0 = e0;
+                sd.fbi = float(2 * (xl + e0) + mb_l) * inv2b_l;
+                return sd;
+            };
+            auto row2 = [&](const int *coords, MRow &st) { row_fn(coords, 0, st); };
+            auto quad = [&](MRow &st, const DSlot &sd, int, const float4 &v, const float4 &gq, int64_t) {
+                const float vals[4] = {v.x, v.y, v.z, v.w};
+                const float gs[4] = {gq.x, gq.y, gq.z, gq.w};
+                float res[4];
+                map4(st, vals, sd.fbi, res);
+                float t = 0.0f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (sd.e0 + e >= 0 && sd.e0 + e < L) t = fmaf(gs[e], res[e], t);
+                kadd(t);
+            };
+            walk_tile<D, QM, 4, MRow, DSlot, true>(in, gout, stride, box_lo, len, r0, r1, ts, true, slot,
+                                                   row2, quad);
+        } else {
+            auto quad_fn = [&](MRow &st, const QuadRef &q) {
+                if (!q.has) return;
+                const float vals[4] = {q.v.x, q.v.y, q.v.z, q.v.w};
+                const float gs[4] = {q.v2.x, q.v2.y, q.v2.z, q.v2.w};
+                float res[4];
+                map4(st, vals, float(2 * (xl + q.e0) + mb_l) * inv2b_l, res);
+                float t = 0.0f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (q.e0 + e >= 0 && q.e0 + e < L) t = fmaf(gs[e], res[e], t);
+                kadd(t);
+            };
+            walk_box<D, (ADAPTIVE && D >= 3) ? 2 : 4, MRow, true>(in, gout, g.N, stride, box_lo, len, r0,
+                                                                  r1, same_align, true, row_fn, quad_fn);
+        }
+        *dot = make_float2(ks, kc);
+        return;
+    }
+
     if constexpr (WALK == kWalkTma) {
         // Warp-specialised tile pipeline: warps 0..7 map (kTmaConsumers
         // threads), warp 8 moves tiles.  Stage s has a "full" barrier (the
@@ -422,6 +484,7 @@ __device__ __forceinline__ void map_cell(const Geom &g, const float *__restrict_
         // stage).  The producer stores a finished full tile back with TMA, waits
         // for the store to have read the stage, then loads the next tile into it.
         static_assert(D >= 3 && REPL, "TMA tiles: 3- and 4-D cells, replicated tables");
+        static_assert(std::is_same<T, float>::value, "TMA tiles: float32 volumes (results in place)");
         constexpr int NS = kTmaStages;
         constexpr int NCW = kTmaConsumers / 32;                 // consumer warps
         constexpr int QT = kTmaTileFloats / 4 / kTmaConsumers;  // quad slots per consumer thread

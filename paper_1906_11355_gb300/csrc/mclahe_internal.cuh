@@ -84,7 +84,9 @@ struct Tuning {
     int map_tma;        // 1: stream 3- and 4-D cells as TMA tiles (where map_tma_box allows)
     int map_flat;       // 1: map_chunks shares per cell dealt out to a persistent grid
     int hist_walk;      // rows of the histogram pass: 0 cp.async ring, 1 TMA tiles (where
-                        // hist_tma_box allows), 2 per-thread loads (least shared memory)
+                        // hist_tma_box allows), 2 per-thread loads (least shared memory),
+                        // 3 the kernel's footprint staged in shared memory (one kernel per
+                        // cluster, where hist_staged_fits allows)
     int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)
 };
 
@@ -404,17 +406,46 @@ struct QuadRef {
     bool has;   // overlaps the row
 };
 
-__device__ __forceinline__ float4 load_quad4(const float *__restrict__ in, int64_t a, int64_t N,
+// ---------------------------------------------------------------------------
+// Input elements.  Volumes are float32, or unsigned 8- or 16-bit integers whose
+// intensities are the integers themselves (converted to fp32 exactly).  A quad
+// is four consecutive elements starting on a multiple of 4 (16, 8 or 4 bytes,
+// aligned); every helper returns fp32 values.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 u16x4(uint2 w) {
+    return make_float4(float(w.x & 0xffffu), float(w.x >> 16), float(w.y & 0xffffu), float(w.y >> 16));
+}
+__device__ __forceinline__ float4 u8x4(uint32_t w) {
+    return make_float4(float(w & 0xffu), float((w >> 8) & 0xffu), float((w >> 16) & 0xffu), float(w >> 24));
+}
+// the quad at p (read-only path; `cs`: streaming, evict first)
+__device__ __forceinline__ float4 ldq(const float *p, bool cs) {
+    return cs ? __ldcs(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+}
+__device__ __forceinline__ float4 ldq(const uint16_t *p, bool cs) {
+    return u16x4(cs ? __ldcs(reinterpret_cast<const uint2 *>(p)) : __ldg(reinterpret_cast<const uint2 *>(p)));
+}
+__device__ __forceinline__ float4 ldq(const uint8_t *p, bool cs) {
+    return u8x4(cs ? __ldcs(reinterpret_cast<const unsigned int *>(p))
+                   : __ldg(reinterpret_cast<const unsigned int *>(p)));
+}
+__device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld1(const uint16_t *p) { return float(__ldg(p)); }
+__device__ __forceinline__ float ld1(const uint8_t *p) { return float(__ldg(p)); }
+template <typename T>
+constexpr uint32_t quad_bytes() { return 4u * uint32_t(sizeof(T)); }
+
+template <typename T>
+__device__ __forceinline__ float4 load_quad4(const T *__restrict__ in, int64_t a, int64_t N,
                                              bool has, bool stream) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (has) {
         if (a + 4 <= N) {
-            v = stream ? __ldcs(reinterpret_cast<const float4 *>(in + a))
-                       : __ldg(reinterpret_cast<const float4 *>(in + a));
+            v = ldq(in + a, stream);
         } else {
-            v.x = in[a];
-            if (a + 1 < N) v.y = in[a + 1];
-            if (a + 2 < N) v.z = in[a + 2];
+            v.x = ld1(in + a);
+            if (a + 1 < N) v.y = ld1(in + a + 1);
+            if (a + 2 < N) v.z = ld1(in + a + 2);
         }
     }
     return v;
@@ -424,8 +455,8 @@ __device__ __forceinline__ float4 load_quad4(const float *__restrict__ in, int64
 // prepares per-row state S; quad_fn(S &state, const QuadRef &q) consumes one
 // quad.  Template parameter RU must equal shape.ru.  With TWO, the same quads
 // of a second array in2 (same layout) are loaded into QuadRef::v2.
-template <int D, int U, int RU, typename S, bool TWO, typename RowFn, typename QuadFn>
-__device__ __forceinline__ void walk_rows(const float *__restrict__ in,
+template <int D, int U, int RU, typename S, bool TWO, typename T, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_rows(const T *__restrict__ in,
                                           const float *__restrict__ in2, int64_t N,
                                           const int64_t *stride, const int *box_lo,
                                           const int *box_len, int r0, int r1,
@@ -484,21 +515,21 @@ __device__ __forceinline__ void walk_rows(const float *__restrict__ in,
 }
 
 // Dispatch of walk_rows on the shape's RU.
-template <int D, int U, typename S, bool TWO = false, typename RowFn, typename QuadFn>
-__device__ __forceinline__ void walk_box(const float *__restrict__ in,
+template <int D, int U, typename S, bool TWO = false, typename T, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_box(const T *__restrict__ in,
                                          const float *__restrict__ in2, int64_t N,
                                          const int64_t *stride, const int *box_lo,
                                          const int *box_len, int r0, int r1, bool same_align,
                                          bool stream, RowFn row_fn, QuadFn quad_fn) {
     const WalkShape ws = walk_shape(box_len[D - 1], box_lo[D - 1], same_align, blockDim.x, U);
     if (ws.ru == 1)
-        walk_rows<D, U, 1, S, TWO>(in, in2, N, stride, box_lo, box_len, r0, r1, ws, stream,
+        walk_rows<D, U, 1, S, TWO, T>(in, in2, N, stride, box_lo, box_len, r0, r1, ws, stream,
                                    row_fn, quad_fn);
     else if (U >= 4 && ws.ru == 4)
-        walk_rows<D, U, (U >= 4 ? 4 : 1), S, TWO>(in, in2, N, stride, box_lo, box_len, r0, r1, ws,
+        walk_rows<D, U, (U >= 4 ? 4 : 1), S, TWO, T>(in, in2, N, stride, box_lo, box_len, r0, r1, ws,
                                                   stream, row_fn, quad_fn);
     else
-        walk_rows<D, U, 2, S, TWO>(in, in2, N, stride, box_lo, box_len, r0, r1, ws, stream,
+        walk_rows<D, U, 2, S, TWO, T>(in, in2, N, stride, box_lo, box_len, r0, r1, ws, stream,
                                    row_fn, quad_fn);
 }
 
@@ -547,8 +578,8 @@ __device__ __forceinline__ TileShape tile_shape(int L, int head, int nthreads, i
 // FULL: every slot of every row is a whole quad inside the box (checked by the
 // caller): no per-slot tests.
 template <int D, int QMAX, int U, typename S, typename SD, bool TWO, bool PF = false,
-          bool FULL = false, typename SlotFn, typename RowFn, typename QuadFn>
-__device__ __forceinline__ void walk_tile(const float *__restrict__ in,
+          bool FULL = false, typename T, typename SlotFn, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_tile(const T *__restrict__ in,
                                           const float *__restrict__ in2, const int64_t *stride,
                                           const int *box_lo, const int *box_len, int r0, int r1,
                                           const TileShape &t, bool stream, SlotFn slot_fn,
@@ -582,8 +613,7 @@ __device__ __forceinline__ void walk_tile(const float *__restrict__ in,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (FULL || ok[i0 + u]) {
-                const float4 *q = reinterpret_cast<const float4 *>(in + a0 + (i0 + u) * step);
-                v[u] = stream ? __ldcs(q) : __ldg(q);
+                v[u] = ldq(in + a0 + (i0 + u) * step, stream);
                 if (TWO) v2[u] = __ldcs(reinterpret_cast<const float4 *>(in2 + a0 + (i0 + u) * step));
             }
         }
@@ -663,15 +693,38 @@ __device__ __forceinline__ float4 lds128(uint32_t addr) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// the quad at src copied to shared memory at dst (16, 8 or 4 bytes), and the
+// fp32 values of a quad copied there
+__device__ __forceinline__ void cpq(uint32_t dst, const float *src) { cp_async16(dst, src); }
+__device__ __forceinline__ void cpq(uint32_t dst, const uint16_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpq(uint32_t dst, const uint8_t *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ float4 ldsq(uint32_t addr) {
+    if constexpr (sizeof(T) == 4) {
+        return lds128(addr);
+    } else if constexpr (sizeof(T) == 2) {
+        uint2 w;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(w.x), "=r"(w.y) : "r"(addr));
+        return u16x4(w);
+    } else {
+        uint32_t w;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(addr));
+        return u8x4(w);
+    }
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // FULL: the caller has checked that every slot of every row is a whole quad
 // inside the box (head 0, L = 4 * LPR * QMAX): no per-slot tests.
-template <int D, int QMAX, int ST, typename S, typename SD, bool FULL = false, typename SlotFn,
-          typename RowFn, typename QuadFn>
-__device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, const int64_t *stride,
+template <int D, int QMAX, int ST, typename S, typename SD, bool FULL = false, typename T,
+          typename SlotFn, typename RowFn, typename QuadFn>
+__device__ __forceinline__ void walk_tile_async(const T *__restrict__ in, const int64_t *stride,
                                                 const int *box_lo, const int *box_len, int r0,
                                                 int r1, const TileShape &t, float4 *ring,
                                                 SlotFn slot_fn, RowFn row_fn, QuadFn quad_fn) {
@@ -711,7 +764,7 @@ __device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, co
         const int64_t a0 = row_addr(iss, coords);
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
-            if (FULL || ok[i]) cp_async16(slot_addr(stage, i), in + a0 + i * step);
+            if (FULL || ok[i]) cpq(slot_addr(stage, i), in + a0 + i * step);
     };
 #pragma unroll
     for (int k = 0; k < ST - 1; ++k) {
@@ -730,7 +783,7 @@ __device__ __forceinline__ void walk_tile_async(const float *__restrict__ in, co
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
             if (FULL || ok[i]) {
-                const float4 v = lds128(slot_addr(stage_c, i));
+                const float4 v = ldsq<T>(slot_addr(stage_c, i));
                 quad_fn(st, sd[i], i, v, v, a0 + i * step);
             }
         stage_c = (stage_c + 1 == ST) ? 0 : stage_c + 1;
@@ -776,7 +829,13 @@ cudaError_t launch_backward(const mclahe_plan_s &p, const float *in, const float
 // backward scratch: int64 table-gradient sums [cells][2^D][LS], the max |g|
 // key (and padding), dL/dT[K]
 size_t bwd_sum_words(const Geom &g);
-size_t bwd_scratch_bytes(const Geom &g);
+size_t bwd_scratch_bytes(const Geom &g, int chunks);
+// k_bwd_gather.cu: the clip-limit gradient alone (d lut/dT tables interpolated
+// like the mapping pass and dotted with the upstream gradient) and its scratch
+size_t bwd_gather_bytes(const Geom &g, int chunks);
+cudaError_t launch_backward_gather(const mclahe_plan_s &p, const float *in, const float *gout,
+                                   unsigned char *ws, const float *d_clip, float *d_grad_clip,
+                                   cudaStream_t st);
 // Dynamic shared memory of a histogram CTA for a row walk (0: per-thread
 // loads, the batched launch; 1: the cp.async row ring; 2: TMA tiles), and of
 // the flat form's range pass.
@@ -786,6 +845,9 @@ size_t hist_range_smem_bytes(int group, int walk, int threads);
 // 2 per-thread loads)
 inline int hist_walk_code(int hist_walk) { return hist_walk == 0 ? 1 : hist_walk == 1 ? 2 : 0; }
 bool hist_tma_box(const Geom &g, int group, int &bx, int &by);
+// the staged walk (hist_walk = 3): fits for R copies and clusters of C CTAs
+// (2- to 4-D, last extent a multiple of 4), with its shared-memory bytes
+bool hist_staged_fits(const Geom &g, int R, int C, size_t *bytes);
 // Tensor map of a float32 volume (dims innermost first) with box[0..D-1]
 // elements per tile (tma_host.cu).
 cudaError_t encode_tensor_map(CUtensorMap *m, const float *ptr, const Geom &g, const int *box);

@@ -121,7 +121,7 @@ Layout make_layout(const Geom &g, const Tuning &t) {
     // backward: partial table gradients (2^D corner tables per cell chunk)
     // and per-kernel threshold gradients
     L.scratch = off;
-    L.scratch_bytes = bwd_scratch_bytes(g);
+    L.scratch_bytes = bwd_scratch_bytes(g, t.bwd_chunks);
     off = align_up(off + L.scratch_bytes);
     L.total = off;
     return L;
@@ -323,11 +323,18 @@ mclahe_status mclahe_plan_set_shapes(mclahe_plan_t p, int32_t hist_group, int32_
     int bx, by, bz;
     if (map_tma != 0 && (map_tma != 1 || !map_tma_box(g, bx, by, bz))) return MCLAHE_ERR_INVALID_ARG;
     if (map_flat != 0 && (map_flat != 1 || map_tma != 0)) return MCLAHE_ERR_INVALID_ARG;
-    if (hist_walk < 0 || hist_walk > 2 || (hist_walk == 1 && !hist_tma_box(g, hist_group, bx, by)))
+    if (hist_walk < 0 || hist_walk > 3 || (hist_walk == 1 && !hist_tma_box(g, hist_group, bx, by)))
         return MCLAHE_ERR_INVALID_ARG;
     if (hist_threads != 256 && !(hist_threads == 512 && g.D >= 4)) return MCLAHE_ERR_INVALID_ARG;
-    if (hist_smem_bytes(g, hist_copies, hist_group, hist_walk_code(hist_walk), hist_threads) > 220 * 1024)
+    if (hist_walk == 3) {
+        // one kernel per cluster of 256-thread CTAs, its footprint in shared memory
+        if (hist_group != 1 || hist_shares != 0 || hist_threads != 256 ||
+            !hist_staged_fits(g, hist_copies, hist_cluster, nullptr))
+            return MCLAHE_ERR_INVALID_ARG;
+    } else if (hist_smem_bytes(g, hist_copies, hist_group, hist_walk_code(hist_walk), hist_threads) >
+               220 * 1024) {
         return MCLAHE_ERR_INVALID_ARG;
+    }
     p->t.hist_group = hist_group;
     p->t.hist_chunks = hist_cluster;
     p->t.hist_copies = hist_copies;

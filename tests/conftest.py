@@ -18,3 +18,13 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def nat():
+    """The built library's binding (host calls only unless a test is marked gpu)."""
+    from paper_1906_11355_gb300 import build, _native
+
+    build.build()
+    _native.load()
+    return _native

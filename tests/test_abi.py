@@ -10,15 +10,6 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-@pytest.fixture(scope="module")
-def nat():
-    from paper_1906_11355_gb300 import build, _native
-
-    build.build()
-    _native.load()
-    return _native
-
-
 def _declared_symbols():
     text = open(os.path.join(ROOT, "include", "mclahe.h")).read()
     return sorted(set(re.findall(r"MCLAHE_API\s+[\w\s\*]*?\b(mclahe_\w+)\s*\(", text)))
@@ -137,12 +128,21 @@ def test_set_shapes_validates_and_round_trips(nat):
     assert nat.mclahe_plan_query(plan)["hist_walk"] == 2
     nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=1)
     assert nat.mclahe_plan_query(plan)["hist_walk"] == 1
-    for bad_walk in (-1, 3):
+    for bad_walk in (-1, 4):
         with pytest.raises(nat.MclaheError):
             nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=bad_walk)
     nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 0, hist_walk=2)
     with pytest.raises(nat.MclaheError):
         nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 0, hist_walk=1)
+    # staged footprints (3): one kernel per cluster, 256-thread CTAs, aligned rows,
+    # and the cluster's share of the footprint within the shared memory
+    nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=3)
+    assert nat.mclahe_plan_query(plan)["hist_walk"] == 3
+    for args in ((2, 4, 16, 0), (1, 1, 16, 0), (1, 1, 8, 4)):   # G = 2; 256 KiB in one CTA; flat
+        with pytest.raises(nat.MclaheError):
+            nat.mclahe_plan_set_shapes(plan, *args, 1, 0, hist_walk=3)
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_plan_set_shapes(odd, 1, 1, 8, 0, 1, 0, hist_walk=3)
     nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1, 0, hist_walk=0)
     # 512-thread histogram CTAs only for 4-D volumes
     with pytest.raises(nat.MclaheError):

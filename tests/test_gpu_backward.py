@@ -183,3 +183,46 @@ def test_backward_integer_sums_are_deterministic_and_scale_free(torch_cuda):
         torch.cuda.synchronize()
         assert torch.equal(s[0], a[0] * 2.0 ** p), p
         assert torch.equal(s[1], a[1] * 2.0 ** p), p
+
+
+@pytest.mark.parametrize("case", CASES, ids=[str(c[0]) + ("A" if c[4] else "G") for c in CASES])
+def test_clip_gradient_alone_gather_matches_oracle_and_scatter(torch_cuda, orc, case):
+    """Without table gradients mclahe_backward takes the gather form (d lut/dT
+    tables interpolated like the mapping pass, dotted with g): the same clip
+    gradient as the oracle's reverse mode and as the scatter form, repeatable
+    bit for bit, and 0 for a clip limit outside [0, 1]."""
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    shape, ks, nb, clip, adaptive = case
+    rng = np.random.default_rng(hash((shape, ks, nb, 9)) % 2**32)
+    x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
+    g = rng.normal(size=shape).astype(np.float32)
+    clip = f32(clip)
+    op = MCLAHE(x.shape, ks, n_bins=nb, clip_limit=clip, adaptive=adaptive)
+    xd = torch.from_numpy(x).cuda()
+    gd = torch.from_numpy(g).cuda()
+    op.forward(xd)
+    got = []
+    for _ in range(2):
+        gc = torch.empty(1, dtype=torch.float32, device="cuda")
+        nat.mclahe_backward(op.plan, xd, gd, op.ws, op.ws_bytes, None, None, gc)
+        got.append(gc.clone())
+    glut = torch.empty(op.n_kernels * nb, dtype=torch.float32, device="cuda")
+    gsc = torch.empty(1, dtype=torch.float32, device="cuda")
+    nat.mclahe_backward(op.plan, xd, gd, op.ws, op.ws_bytes, None, glut, gsc)
+    torch.cuda.synchronize()
+    assert torch.equal(got[0], got[1])
+    _, want = orc.mclahe_backward(x, ks, nb, clip, g.astype(np.float64), mode=int(adaptive))
+    want_lut, _ = orc.mclahe_backward(x, ks, nb, clip, g.astype(np.float64), mode=int(adaptive))
+    tol = REL * max(abs(want), 1e-3 * np.abs(want_lut).max())
+    assert abs(got[0].item() - want) <= tol, (got[0].item(), want)
+    assert abs(got[0].item() - gsc.item()) <= tol, (got[0].item(), gsc.item())
+    # a clip limit outside [0, 1] is clamped by the forward pass: zero gradient
+    out_clip = torch.tensor([1.5], device="cuda")
+    op.forward(xd, clip=out_clip)
+    gc = torch.empty(1, dtype=torch.float32, device="cuda")
+    nat.mclahe_backward(op.plan, xd, gd, op.ws, op.ws_bytes, out_clip, None, gc)
+    torch.cuda.synchronize()
+    assert gc.item() == 0.0

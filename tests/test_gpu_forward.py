@@ -354,3 +354,34 @@ def test_workload_full_size_every_mapping_walk(torch_cuda, workload_cache, name)
         op.set_shapes(**{**tuned, **walk})
         out.fill_(-1.0)
         check_full(torch_cuda, op, xd, want, aux, out=out)
+
+
+# the staged histogram walk (hist_walk = 3): every kernel's footprint copied into
+# the shared memory of its cluster once; 2- to 4-D, both range modes, edge
+# kernels with mirror multiplicities 2 and 3 (b not dividing s), clusters of 1-8
+STAGED_CASES = [
+    ((64, 64), (16, 16), 256, 0.02, False),
+    ((40, 56), (5, 7), 64, 0.03, True),
+    ((16, 64, 64), (4, 16, 16), 256, 0.02, True),
+    ((13, 37, 36), (4, 6, 12), 256, 0.02, False),
+    ((19, 23, 28), (5, 4, 7), 100, 0.02, True),
+    ((6, 10, 12, 16), (3, 5, 4, 8), 512, 0.01, False),
+    ((9, 11, 14, 20), (3, 4, 5, 4), 50, 0.05, True),
+]
+
+
+@pytest.mark.parametrize("cluster,copies", [(1, 32), (2, 8), (4, 16), (8, 2)])
+@pytest.mark.parametrize("case", STAGED_CASES,
+                         ids=[str(c[0]) + ("A" if c[4] else "G") for c in STAGED_CASES])
+def test_staged_histogram_walk_matches_oracle(torch_cuda, orc, case, cluster, copies):
+    from paper_1906_11355_gb300 import _native as nat
+
+    shape, ks, nb, clip, adaptive = case
+    rng = np.random.default_rng(hash((shape, ks, nb, cluster, 3)) % 2**32)
+    x = rng.gamma(2.0, 1.0, size=shape).astype(np.float32)
+    x[rng.random(size=shape) < 0.2] = 0.0
+    shapes = dict(hist_group=1, hist_cluster=cluster, hist_copies=copies, hist_shares=0,
+                  map_chunks=1, hist_walk=3)
+    op, _, _ = run_case(torch_cuda, orc, x, ks, nb, clip, adaptive, shapes=shapes)
+    assert op.shapes()["hist_walk"] == 3
+    assert nat.mclahe_sync_status(op.ws) == 0

@@ -375,6 +375,8 @@ def measure_batched(dev, steps, warmup):
             op.forward(x, out=o)
 
     ms_plain = _time_steps(plain, steps, warmup, stream)
+    ms_conc = _time_steps(lambda: batch.forward(xs, outs=outs, use_graph=True, concurrent=8), steps, warmup,
+                          stream)
     launches = {"plain": 0}
     from paper_1906_11355_gb300 import _native as nat
 
@@ -387,6 +389,9 @@ def measure_batched(dev, steps, warmup):
             "value": voxels / (ms_batch * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms_batch,
             "plain_forward_ms": ms_plain, "plain_forward_value": voxels / (ms_plain * 1e-3) / 1e9,
             "speedup_vs_plain_forward": ms_plain / ms_batch,
+            "concurrent": {"call": "mclahe_batch_concurrent (8 graph branches, each volume's own forward)",
+                           "ms_per_step": ms_conc, "value": voxels / (ms_conc * 1e-3) / 1e9,
+                           "speedup_vs_plain_forward": ms_plain / ms_conc},
             "launches": {"batched": groups, "plain_forward": launches["plain"]},
             "data": "synthetic, drawn on the device (torch generators, seeds 1000+v)"}
 

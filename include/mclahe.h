@@ -222,6 +222,35 @@ MCLAHE_API mclahe_status mclahe_forward_typed(mclahe_plan_t plan, mclahe_dtype d
                                               float *d_out, void *d_ws, size_t ws_bytes,
                                               const float *d_clip, mclahe_stream_t stream);
 
+/*
+ * mclahe_forward_chunked -- Algorithm 1 on a float32 volume held in HOST memory,
+ * streamed through a device staging buffer in slabs along dimension 0, for
+ * volumes larger than the device (no counterpart in the paper, which names
+ * holding the whole dataset in memory as its main limitation, Sec. V).
+ * Slabs are cut on kernel boundaries: a global-range sweep (global range not
+ * given), a histogram sweep in which each slab holds the whole footprints of a
+ * run of kernel rows (their histograms and tables complete in it), then a
+ * mapping sweep over runs of cell rows whose output slabs are copied back.
+ * The result equals mclahe_forward's (the same kernels, on slabs).
+ *   h_in, h_out   host, prod(shape) float32 each (pinned memory lets the
+ *                 copies run at full speed), distinct.
+ *   d_ws          device workspace as for mclahe_forward (all K tables live in it).
+ *   d_stage       device staging buffer of stage_bytes, 256-byte aligned; it
+ *                 must hold two slabs of the widest kernel footprint along
+ *                 dimension 0 (MCLAHE_ERR_WORKSPACE otherwise).
+ *   d_clip        nullable device clip limit, as for mclahe_forward.
+ * The histogram pass runs in its cluster form with the cp.async row ring and
+ * the mapping pass on its per-cell grid.  2- to 4-D volumes.  Copies and
+ * kernels run in order on `stream`; the call returns once all are enqueued
+ * (h_out is complete when the stream is).
+ * Returns MCLAHE_OK, MCLAHE_ERR_INVALID_ARG, MCLAHE_ERR_UNSUPPORTED (1-D),
+ * MCLAHE_ERR_WORKSPACE, MCLAHE_ERR_CUDA.
+ */
+MCLAHE_API mclahe_status mclahe_forward_chunked(mclahe_plan_t plan, const float *h_in, float *h_out,
+                                                void *d_ws, size_t ws_bytes, void *d_stage,
+                                                size_t stage_bytes, const float *d_clip,
+                                                mclahe_stream_t stream);
+
 /* The passes of mclahe_forward, in the order it runs them. */
 typedef enum {
     MCLAHE_PASS_CLEAR = 0,  /* zero what later passes accumulate with atomics (memset): the
@@ -252,6 +281,40 @@ MCLAHE_API mclahe_status mclahe_forward_pass(mclahe_plan_t plan, mclahe_pass pas
 /* Number of this library's kernels a pass launches for this plan (0 for
  * CLEAR, which is a memset, and for RANGE with a caller-given global range). */
 MCLAHE_API int mclahe_pass_launches(mclahe_plan_t plan, mclahe_pass pass);
+
+/*
+ * Slabs of one volume along dimension 0 (no counterpart in the paper; the
+ * building blocks of mclahe_forward_chunked and of splitting one volume across
+ * devices, partitioned in slabs with a one-row table halo).
+ *
+ * mclahe_slab_rows -- host only: the original rows [*first_row, *end_row) along
+ * dimension 0 that a slab must hold for
+ *   MCLAHE_PASS_RANGE  rows [row0, row1) themselves;
+ *   MCLAHE_PASS_HIST   the kernel rows [row0, row1): the union of their
+ *                      footprints (Sec. III.B, mirror images included);
+ *   MCLAHE_PASS_MAP    the cell rows [row0, row1) (cell c lies between kernel
+ *                      rows c and c + 1, Sec. III.C).
+ *
+ * mclahe_forward_slab -- one pass on a slab: d_slab holds the volume's elements
+ * from slab_first on (a multiple of 4, at most first_row * row elements, 16-byte
+ * aligned pointer), d_out_slab (MAP only) the output elements from slab_first on.
+ *   RANGE  min/max of rows [row0, row1) added to the workspace's global range
+ *          keys (global range not given; clear them first, and combine the
+ *          keys of several devices by a maximum of each word);
+ *   HIST   histograms and tables of the kernel rows [row0, row1) (a global
+ *          range must already be in the keys);
+ *   MAP    the cell rows [row0, row1), whose tables (kernel rows row0..row1,
+ *          table rows, ranges lo and scale) must be in the workspace.
+ * Kernel row k's tables are the contiguous workspace rows k K1 .. (k + 1) K1 - 1
+ * of lut, lo and scale (K1 = K / n[0] kernels per row, mclahe_plan_info).
+ * Returns MCLAHE_OK, MCLAHE_ERR_INVALID_ARG, MCLAHE_ERR_WORKSPACE, MCLAHE_ERR_CUDA.
+ */
+MCLAHE_API mclahe_status mclahe_slab_rows(mclahe_plan_t plan, mclahe_pass pass, int32_t row0,
+                                          int32_t row1, int64_t *first_row, int64_t *end_row);
+MCLAHE_API mclahe_status mclahe_forward_slab(mclahe_plan_t plan, mclahe_pass pass, const float *d_slab,
+                                             int64_t slab_first, float *d_out_slab, void *d_ws,
+                                             size_t ws_bytes, const float *d_clip, int32_t row0,
+                                             int32_t row1, mclahe_stream_t stream);
 
 /*
  * mclahe_backward -- adjoint of mclahe_forward (no counterpart in the paper,
@@ -298,6 +361,22 @@ MCLAHE_API mclahe_status mclahe_batch(int n_vol, const mclahe_plan_t *plans, con
 
 /* Workspace bytes mclahe_batch needs for these plans. */
 MCLAHE_API size_t mclahe_batch_workspace_bytes(int n_vol, const mclahe_plan_t *plans);
+
+/*
+ * mclahe_batch_concurrent -- the same batch as mclahe_batch (same arguments and
+ * workspace), run as every volume's own forward pass -- its plan's launch
+ * shapes and walks, so each output equals mclahe_forward's bit for bit -- on
+ * `branches` (1..16) parallel branches forked from `stream` and joined back
+ * into it, the volumes dealt longest first to the least loaded branch.  Small
+ * volumes and the tails of passes then overlap instead of running one after
+ * another.  With use_graph != 0 the whole fork-join is captured once per
+ * (plans, pointers, branches) into a cached CUDA graph and replayed.  No
+ * counterpart in the paper.  Returns as mclahe_batch.
+ */
+MCLAHE_API mclahe_status mclahe_batch_concurrent(int n_vol, const mclahe_plan_t *plans,
+                                                 const float *const *d_in, float *const *d_out,
+                                                 void *d_ws, size_t ws_bytes, const float *d_clip,
+                                                 mclahe_stream_t stream, int branches, int use_graph);
 
 /*
  * mclahe_batch_set_wait -- the bounded waits of mclahe_batch's persistent

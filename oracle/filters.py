@@ -57,8 +57,9 @@ def gaussian(x, sigma):
 
 
 def gaussian_weights_fp32(sigma):
-    """The fp32 weights the exact form uses: the FP64 weights rounded to fp32."""
-    w, r = gaussian_weights(sigma)
+    """The fp32 weights the exact form uses: sigma taken as an fp32 value (the
+    interface passes it as float), the FP64 weights of it rounded to fp32."""
+    w, r = gaussian_weights(float(np.float32(sigma)))
     return w.astype(np.float32), r
 
 

@@ -36,7 +36,8 @@ EXPORTS = (
     "mclahe_plan_set_shapes", "mclahe_forward_graph", "mclahe_noalloc_sync_status",
     "mclahe_batch_set_wait", "mclahe_forward_typed", "mclahe_metrics",
     "mclahe_metrics_workspace_bytes", "mclahe_gaussian_weights", "mclahe_filter_gaussian",
-    "mclahe_filter_median",
+    "mclahe_filter_median", "mclahe_forward_chunked", "mclahe_slab_rows", "mclahe_forward_slab",
+    "mclahe_batch_concurrent",
 )
 
 MCLAHE_F32, MCLAHE_U16, MCLAHE_U8 = 0, 1, 2
@@ -117,6 +118,9 @@ def load(path: str = LIB_PATH):
         lib.mclahe_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), vp, sz, vp, vp, ctypes.c_int]
         lib.mclahe_batch.restype = ctypes.c_int
+        lib.mclahe_batch_concurrent.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                ctypes.POINTER(vp), vp, sz, vp, vp, ctypes.c_int, ctypes.c_int]
+        lib.mclahe_batch_concurrent.restype = ctypes.c_int
         lib.mclahe_batch_workspace_bytes.argtypes = [ctypes.c_int, ctypes.POINTER(vp)]
         lib.mclahe_batch_workspace_bytes.restype = sz
         lib.mclahe_autotune.argtypes = [vp, vp, vp, vp, sz, vp]
@@ -131,6 +135,13 @@ def load(path: str = LIB_PATH):
         lib.mclahe_pass_launches.restype = ctypes.c_int
         lib.mclahe_forward_noalloc.argtypes = [vp, vp, vp, vp, vp]
         lib.mclahe_forward_noalloc.restype = ctypes.c_int
+        lib.mclahe_slab_rows.argtypes = [vp, ctypes.c_int, i32, i32, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int64)]
+        lib.mclahe_slab_rows.restype = ctypes.c_int
+        lib.mclahe_forward_slab.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, vp, vp, sz, vp, i32, i32, vp]
+        lib.mclahe_forward_slab.restype = ctypes.c_int
+        lib.mclahe_forward_chunked.argtypes = [vp, vp, vp, vp, sz, vp, sz, vp, vp]
+        lib.mclahe_forward_chunked.restype = ctypes.c_int
         lib.mclahe_gaussian_weights.argtypes = [f32, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.mclahe_gaussian_weights.restype = ctypes.c_int
         lib.mclahe_filter_gaussian.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
@@ -306,6 +317,31 @@ def mclahe_filter_median(d_in, d_out, shape, size, stream=None):
            "mclahe_filter_median")
 
 
+def mclahe_slab_rows(plan, pass_, row0, row1):
+    """Original rows (first, end) along dimension 0 a slab needs for a pass."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().mclahe_slab_rows(plan.handle, int(pass_), int(row0), int(row1), ctypes.byref(a),
+                                   ctypes.byref(b)), "mclahe_slab_rows")
+    return int(a.value), int(b.value)
+
+
+def mclahe_forward_slab(plan, pass_, d_slab, slab_first, d_out_slab, d_ws, ws_bytes, row0, row1,
+                        d_clip=None, stream=None):
+    """One pass (RANGE, HIST or MAP) on a slab of the volume along dimension 0."""
+    st = load().mclahe_forward_slab(plan.handle, int(pass_), _ptr(d_slab), int(slab_first), _ptr(d_out_slab),
+                                    _ptr(d_ws), int(ws_bytes), _ptr(d_clip), int(row0), int(row1),
+                                    _stream(stream))
+    _check(st, "mclahe_forward_slab")
+
+
+def mclahe_forward_chunked(plan, h_in, h_out, d_ws, ws_bytes, d_stage, stage_bytes, d_clip=None,
+                           stream=None):
+    """Forward pass of a host-resident float32 volume streamed through d_stage."""
+    st = load().mclahe_forward_chunked(plan.handle, _ptr(h_in), _ptr(h_out), _ptr(d_ws), int(ws_bytes),
+                                       _ptr(d_stage), int(stage_bytes), _ptr(d_clip), _stream(stream))
+    _check(st, "mclahe_forward_chunked")
+
+
 def mclahe_forward_noalloc(plan, d_in, d_out, d_clip=None, stream=None):
     """Forward pass using the library's built-in scratch array (allocates nothing)."""
     st = load().mclahe_forward_noalloc(plan.handle, _ptr(d_in), _ptr(d_out), _ptr(d_clip),
@@ -359,6 +395,16 @@ def mclahe_batch_set_wait(max_polls=0, unreachable=False):
     wait target out of reach (tests of the timeout path only)."""
     _check(load().mclahe_batch_set_wait(int(max_polls), 1 if unreachable else 0),
            "mclahe_batch_set_wait")
+
+
+def mclahe_batch_concurrent(plans, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None, branches=8,
+                            use_graph=True):
+    n = len(plans)
+    hs = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    st = load().mclahe_batch_concurrent(n, hs, _ptr_array(d_in), _ptr_array(d_out), _ptr(d_ws),
+                                        int(ws_bytes), _ptr(d_clip), _stream(stream), int(branches),
+                                        1 if use_graph else 0)
+    _check(st, "mclahe_batch_concurrent")
 
 
 def mclahe_autotune(plan, d_in, d_out, d_ws, ws_bytes, stream=None):

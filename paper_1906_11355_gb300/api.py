@@ -145,10 +145,13 @@ class MCLAHEBatch:
         self.ws_bytes = nat.mclahe_batch_workspace_bytes(self.plans)
         self.ws = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
 
-    def forward(self, xs, outs=None, clip=None, stream=None, use_graph=True):
+    def forward(self, xs, outs=None, clip=None, stream=None, use_graph=True, concurrent=0):
         """Run MCLAHE on every volume of xs (contiguous float32 CUDA tensors);
         returns outs.  clip: optional float32 CUDA tensor of one clip limit per
-        volume.  With use_graph, calls with the same tensors replay one graph."""
+        volume.  With use_graph, calls with the same tensors replay one graph.
+        concurrent > 0: every volume's own forward pass on that many parallel
+        graph branches (mclahe_batch_concurrent) instead of the persistent
+        work-list launches (mclahe_batch)."""
         if len(xs) != len(self.plans):
             raise ValueError("one input per plan expected")
         for x, s in zip(xs, self.specs):
@@ -158,7 +161,11 @@ class MCLAHEBatch:
                 raise ValueError(f"expected shape {tuple(s['shape'])}, got {tuple(x.shape)}")
         if outs is None:
             outs = [torch.empty_like(x) for x in xs]
-        nat.mclahe_batch(self.plans, xs, outs, self.ws, self.ws_bytes, clip, stream, use_graph)
+        if concurrent:
+            nat.mclahe_batch_concurrent(self.plans, xs, outs, self.ws, self.ws_bytes, clip, stream, concurrent,
+                                        use_graph)
+        else:
+            nat.mclahe_batch(self.plans, xs, outs, self.ws, self.ws_bytes, clip, stream, use_graph)
         return outs
 
     __call__ = forward

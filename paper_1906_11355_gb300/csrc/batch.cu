@@ -246,6 +246,69 @@ mclahe_status replay_cached(GraphKey key, cudaStream_t st, Enqueue &&enqueue) {
     return cudaGraphLaunch(exec, st) == cudaSuccess ? MCLAHE_OK : MCLAHE_ERR_CUDA;
 }
 
+// Side streams and events for the concurrent form, per device, created once
+// and kept for the process (a captured graph's branches must outlive the capture).
+constexpr int kMaxBranches = 16;
+struct BranchPool {
+    cudaStream_t s[kMaxBranches] = {};
+    cudaEvent_t fork = nullptr, join[kMaxBranches] = {};
+    bool ok = false;
+};
+std::mutex g_pool_mutex;
+std::map<int, BranchPool> g_pools;
+
+BranchPool *branch_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    BranchPool &p = g_pools[dev];
+    if (!p.ok) {
+        if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        for (int i = 0; i < kMaxBranches; ++i)
+            if (cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming) != cudaSuccess)
+                return nullptr;
+        p.ok = true;
+    }
+    return &p;
+}
+
+// Every volume's own forward pass (its plan's launch shapes and walks) on one
+// of `branches` parallel branches forked from st and joined back into it;
+// volumes are dealt longest first to the least loaded branch.
+mclahe_status enqueue_concurrent(int n_vol, const mclahe_plan_t *plans, const float *const *d_in,
+                                 float *const *d_out, unsigned char *ws, const float *d_clip,
+                                 cudaStream_t st, int branches) {
+    BranchPool *pool = branch_pool();
+    if (!pool) return MCLAHE_ERR_CUDA;
+    const BatchLayout L = batch_layout(n_vol, plans);
+    branches = std::max(1, std::min({branches, kMaxBranches, n_vol}));
+    std::vector<int> order(n_vol);
+    for (int v = 0; v < n_vol; ++v) order[v] = v;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return plans[a]->g.N > plans[b]->g.N; });
+    std::vector<int64_t> load(branches, 0);
+    std::vector<std::vector<int>> lists(branches);
+    for (int v : order) {
+        const int b = int(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[b].push_back(v);
+        load[b] += plans[v]->g.N;
+    }
+    if (cudaEventRecord(pool->fork, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    for (int b = 0; b < branches; ++b) {
+        cudaStream_t sb = pool->s[b];
+        if (cudaStreamWaitEvent(sb, pool->fork, 0) != cudaSuccess) return MCLAHE_ERR_CUDA;
+        for (int v : lists[b]) {
+            const mclahe_status s = forward_impl(*plans[v], d_in[v], d_out[v], ws + L.vol[v],
+                                                 d_clip ? d_clip + v : nullptr, sb);
+            if (s != MCLAHE_OK) return s;
+        }
+        if (cudaEventRecord(pool->join[b], sb) != cudaSuccess) return MCLAHE_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, pool->join[b], 0) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    }
+    return MCLAHE_OK;
+}
+
 }  // namespace
 
 void batch_forget_plan(const mclahe_plan_s *p) {
@@ -303,6 +366,38 @@ mclahe_status mclahe_batch(int n_vol, const mclahe_plan_t *plans, const float *c
     key.ptrs.push_back(reinterpret_cast<const void *>(uintptr_t(g_wait_unreachable.load())));
     return replay_cached(key, st, [&](cudaStream_t cap) {
         return enqueue_batch(n_vol, plans, d_in, d_out, ws, d_clip, cap);
+    });
+}
+
+mclahe_status mclahe_batch_concurrent(int n_vol, const mclahe_plan_t *plans, const float *const *d_in,
+                                      float *const *d_out, void *d_ws, size_t ws_bytes,
+                                      const float *d_clip, mclahe_stream_t stream, int branches,
+                                      int use_graph) {
+    if (n_vol < 1 || !plans || !d_in || !d_out || branches < 1) return MCLAHE_ERR_INVALID_ARG;
+    for (int v = 0; v < n_vol; ++v) {
+        if (!plans[v] || !d_in[v] || !d_out[v] || d_in[v] == d_out[v]) return MCLAHE_ERR_INVALID_ARG;
+        if ((reinterpret_cast<uintptr_t>(d_in[v]) & 15) || (reinterpret_cast<uintptr_t>(d_out[v]) & 15))
+            return MCLAHE_ERR_INVALID_ARG;
+    }
+    if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & (kWsAlign - 1)) ||
+        ws_bytes < mclahe_batch_workspace_bytes(n_vol, plans))
+        return MCLAHE_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *ws = static_cast<unsigned char *>(d_ws);
+    if (!use_graph) return enqueue_concurrent(n_vol, plans, d_in, d_out, ws, d_clip, st, branches);
+    GraphKey key;
+    // a tag no other key has in its first slot, then the plans and pointers
+    key.ptrs.push_back(reinterpret_cast<const void *>(uintptr_t(2)));
+    for (int v = 0; v < n_vol; ++v) {
+        key.ptrs.push_back(plans[v]);
+        key.ptrs.push_back(d_in[v]);
+        key.ptrs.push_back(d_out[v]);
+    }
+    key.ptrs.push_back(d_ws);
+    key.ptrs.push_back(d_clip);
+    key.ptrs.push_back(reinterpret_cast<const void *>(uintptr_t(branches)));
+    return replay_cached(key, st, [&](cudaStream_t cap) {
+        return enqueue_concurrent(n_vol, plans, d_in, d_out, ws, d_clip, cap, branches);
     });
 }
 

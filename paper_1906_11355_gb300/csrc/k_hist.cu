@@ -90,4 +90,24 @@ cudaError_t launch_hist(const mclahe_plan_s &p, const float *in, unsigned char *
     return launch_any(p, in, ws, d_clip, st, false);
 }
 
+// Items [item0, item0 + nitems) of the cluster form with the cp.async row ring
+// (the plan's groups, clusters and copies; a flat plan runs as one-CTA clusters)
+cudaError_t launch_hist_items(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+                              const float *d_clip, cudaStream_t st, int64_t item0, int64_t nitems) {
+    HistTmaArgs none;
+    std::memset(&none.map, 0, sizeof(none.map));
+    const bool a = p.g.mode == MCLAHE_RANGE_ADAPTIVE;
+    switch (p.g.D) {
+        case 1: return a ? launch_hist_cluster<1, true, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems)
+                         : launch_hist_cluster<1, false, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems);
+        case 2: return a ? launch_hist_cluster<2, true, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems)
+                         : launch_hist_cluster<2, false, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems);
+        case 3: return a ? launch_hist_cluster<3, true, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems)
+                         : launch_hist_cluster<3, false, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems);
+        case 4: return a ? launch_hist_cluster<4, true, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems)
+                         : launch_hist_cluster<4, false, kHistRing, float>(p, in, ws, d_clip, st, none, item0, nitems);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace mclahe

@@ -35,10 +35,10 @@ __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistT
            const T *__restrict__ in, const uint32_t *__restrict__ keys,
            const float *__restrict__ d_clip, uint32_t *__restrict__ hist, float *__restrict__ lut,
            float *__restrict__ lo_out, float *__restrict__ scale_out, int G, int R,
-           uint32_t *status) {
+           uint32_t *status, int64_t item0) {
     extern __shared__ __align__(128) uint32_t sh[];
     __shared__ __align__(8) uint64_t s_tbar[kHistTmaStages];
-    const int64_t item = blockIdx.x / cg::this_cluster().num_blocks();
+    const int64_t item = item0 + blockIdx.x / cg::this_cluster().num_blocks();
     TmaRing<kHistTmaStages> tr{};
     if constexpr (HW == kHistTma)
         tr = tma_ring_init<kHistTmaStages>(s_tbar, hist_tma_stage0(sh, hist_smem_words(g.P, R, G)),
@@ -89,7 +89,8 @@ struct HistTmaArgs {
 
 template <int D, bool ADAPTIVE, int HW, typename T>
 static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const T *in, unsigned char *ws,
-                                       const float *d_clip, cudaStream_t st, const HistTmaArgs &ta) {
+                                       const float *d_clip, cudaStream_t st, const HistTmaArgs &ta,
+                                       int64_t item0 = 0, int64_t nitems = -1) {
     const Geom &g = p.g;
     const int C = p.t.hist_chunks;
     const size_t smem = hist_smem_bytes(g, p.t.hist_copies, p.t.hist_group, HW, p.t.hist_threads);
@@ -97,7 +98,8 @@ static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const T *in, unsi
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), size_t(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(hist_items(g, p.t.hist_group) * C));
+    // items [item0, item0 + nitems) (all by default)
+    cfg.gridDim = dim3(unsigned((nitems < 0 ? hist_items(g, p.t.hist_group) : nitems) * C));
     cfg.blockDim = dim3(p.t.hist_threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -114,7 +116,7 @@ static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const T *in, unsi
                               reinterpret_cast<float *>(ws + p.ws.lut),
                               reinterpret_cast<float *>(ws + p.ws.lo),
                               reinterpret_cast<float *>(ws + p.ws.scale), p.t.hist_group,
-                              p.t.hist_copies, reinterpret_cast<uint32_t *>(ws + p.ws.status));
+                              p.t.hist_copies, reinterpret_cast<uint32_t *>(ws + p.ws.status), item0);
 }
 
 // One launch of a flat form: a persistent grid of as many CTAs as fit on the

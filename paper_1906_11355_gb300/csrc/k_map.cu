@@ -35,4 +35,9 @@ cudaError_t launch_map(const mclahe_plan_s &p, const float *in, float *out,
     return launch_map_any(p, in, out, ws, st);
 }
 
+cudaError_t launch_map_cells(const mclahe_plan_s &p, const float *in, float *out,
+                             const unsigned char *ws, cudaStream_t st, int64_t cell0, int64_t ncells) {
+    return launch_map_any(p, in, out, ws, st, cell0, ncells);
+}
+
 }  // namespace mclahe

@@ -17,11 +17,12 @@ __global__ void __launch_bounds__(256, D >= 4 ? (ADAPTIVE ? 1 : 2) : (ADAPTIVE &
                                              float *__restrict__ out,
                                              const float *__restrict__ lut,
                                              const float *__restrict__ lo_k,
-                                             const float *__restrict__ scale_k, int chunks) {
+                                             const float *__restrict__ scale_k, int chunks, int64_t cell0) {
     extern __shared__ __align__(16) float tab[];
-    const int64_t cell = blockIdx.x / chunks;
-    const int chunk = int(blockIdx.x - cell * chunks);
-    map_cell<D, ADAPTIVE, REPL, kWalkRing, false, T>(g, in, out, lut, lo_k, scale_k, cell, chunk, chunks, tab);
+    const int64_t b = blockIdx.x / chunks;
+    const int chunk = int(blockIdx.x - b * chunks);
+    map_cell<D, ADAPTIVE, REPL, kWalkRing, false, T>(g, in, out, lut, lo_k, scale_k, cell0 + b, chunk, chunks,
+                                                     tab);
 }
 
 // TMA tiles (kWalkTma): the whole cell row along the last dim, as many rows
@@ -109,27 +110,31 @@ static cudaError_t launch_map_flat_t(const mclahe_plan_s &p, const float *in, fl
 template <int D, bool A, bool REPL, typename T>
 static cudaError_t launch_map_t(const mclahe_plan_s &p, const T *in, float *out,
                                 const unsigned char *ws, cudaStream_t st, unsigned grid,
-                                size_t smem) {
+                                size_t smem, int64_t cell0, bool full) {
     if constexpr (std::is_same<T, float>::value) {
-        if (p.t.map_flat) return launch_map_flat_t<D, A, REPL>(p, in, out, ws, st, smem);
+        if (p.t.map_flat && full) return launch_map_flat_t<D, A, REPL>(p, in, out, ws, st, smem);
     }
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_map<D, A, REPL, T>), smem);
     if (e != cudaSuccess) return e;
     k_map<D, A, REPL, T><<<grid, p.t.map_threads, smem, st>>>(
         p.g, in, out, reinterpret_cast<const float *>(ws + p.ws.lut),
         reinterpret_cast<const float *>(ws + p.ws.lo), reinterpret_cast<const float *>(ws + p.ws.scale),
-        p.t.map_chunks);
+        p.t.map_chunks, cell0);
     return cudaGetLastError();
 }
 
+// cells [cell0, cell0 + ncells) (all by default; a part of the cells always
+// takes the per-cell grid with per-thread walks)
 template <int D, typename T>
 static cudaError_t launch_map_d(const mclahe_plan_s &p, const T *in, float *out,
-                                const unsigned char *ws, cudaStream_t st) {
+                                const unsigned char *ws, cudaStream_t st, int64_t cell0 = 0,
+                                int64_t ncells = -1) {
     const Geom &g = p.g;
-    const unsigned grid = unsigned(n_cells(g) * p.t.map_chunks);
+    const bool full = cell0 == 0 && (ncells < 0 || ncells == n_cells(g));
+    const unsigned grid = unsigned((full ? n_cells(g) : ncells) * p.t.map_chunks);
     int bx, by, bz;
     if constexpr (D >= 3 && std::is_same<T, float>::value) {
-        if (p.t.map_tma && map_tma_box(g, bx, by, bz))
+        if (full && p.t.map_tma && map_tma_box(g, bx, by, bz))
             return g.mode == MCLAHE_RANGE_ADAPTIVE
                        ? launch_map_tma_t<D, true>(p, in, out, ws, st, grid, bx, by, bz)
                        : launch_map_tma_t<D, false>(p, in, out, ws, st, grid, bx, by, bz);
@@ -137,20 +142,21 @@ static cudaError_t launch_map_d(const mclahe_plan_s &p, const T *in, float *out,
     const size_t smem = map_smem_bytes(g);
     const bool repl = map_replicated(g);
     if (g.mode == MCLAHE_RANGE_ADAPTIVE)
-        return repl ? launch_map_t<D, true, true, T>(p, in, out, ws, st, grid, smem)
-                    : launch_map_t<D, true, false, T>(p, in, out, ws, st, grid, smem);
-    return repl ? launch_map_t<D, false, true, T>(p, in, out, ws, st, grid, smem)
-                : launch_map_t<D, false, false, T>(p, in, out, ws, st, grid, smem);
+        return repl ? launch_map_t<D, true, true, T>(p, in, out, ws, st, grid, smem, cell0, full)
+                    : launch_map_t<D, true, false, T>(p, in, out, ws, st, grid, smem, cell0, full);
+    return repl ? launch_map_t<D, false, true, T>(p, in, out, ws, st, grid, smem, cell0, full)
+                : launch_map_t<D, false, false, T>(p, in, out, ws, st, grid, smem, cell0, full);
 }
 
 template <typename T>
 static cudaError_t launch_map_any(const mclahe_plan_s &p, const T *in, float *out,
-                                  const unsigned char *ws, cudaStream_t st) {
+                                  const unsigned char *ws, cudaStream_t st, int64_t cell0 = 0,
+                                  int64_t ncells = -1) {
     switch (p.g.D) {
-        case 1: return launch_map_d<1>(p, in, out, ws, st);
-        case 2: return launch_map_d<2>(p, in, out, ws, st);
-        case 3: return launch_map_d<3>(p, in, out, ws, st);
-        case 4: return launch_map_d<4>(p, in, out, ws, st);
+        case 1: return launch_map_d<1>(p, in, out, ws, st, cell0, ncells);
+        case 2: return launch_map_d<2>(p, in, out, ws, st, cell0, ncells);
+        case 3: return launch_map_d<3>(p, in, out, ws, st, cell0, ncells);
+        case 4: return launch_map_d<4>(p, in, out, ws, st, cell0, ncells);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -89,6 +89,15 @@ cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char 
                          cudaStream_t st) {
     return launch_range_t(p, in, ws, st);
 }
+
+// min/max of n contiguous values of a buffer, added to the global range keys
+// (the slabs of mclahe_forward_chunked)
+cudaError_t launch_range_buffer(const float *buf, int64_t n, uint32_t *keys, cudaStream_t st) {
+    const int64_t nq = (n >> 2) + 1;
+    const int blocks = int(std::min<int64_t>((nq + 255) / 256, int64_t(device_sms()) * 4));
+    k_range_global<float><<<blocks, 256, 0, st>>>(buf, n, keys);
+    return cudaGetLastError();
+}
 cudaError_t launch_range_u16(const mclahe_plan_s &p, const uint16_t *in, unsigned char *ws,
                              cudaStream_t st) {
     return launch_range_t(p, in, ws, st);

@@ -3,6 +3,7 @@
 // (converted to fp32, which is exact below 2^24), so the result equals
 // mclahe_forward on the float32 volume of those values; reading 2 or 1 bytes
 // per voxel instead of 4 is what the integer forms save.
+#include <algorithm>
 #include <cstring>
 
 #include "mclahe_internal.cuh"
@@ -86,7 +87,16 @@ mclahe_status forward_int(const mclahe_plan_s &p, const T *in, float *out, unsig
         if (range_of(p, in, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
     }
     if (hist_of(p, in, ws, d_clip, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
-    if (map_of(p, in, out, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
+    // the per-cell mapping grid: a flat plan's shares per cell would each restage
+    // the corner tables, so about two CTAs per SM in all instead
+    mclahe_plan_s q = p;
+    if (q.t.map_flat || q.t.map_tma) {
+        const int64_t cells = n_cells(q.g);
+        q.t.map_chunks = int(std::min<int64_t>(64, std::max<int64_t>(1, (2 * int64_t(device_sms()) + cells - 1) / cells)));
+        q.t.map_flat = 0;
+        q.t.map_tma = 0;
+    }
+    if (map_of(q, in, out, ws, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
     return MCLAHE_OK;
 }
 

@@ -166,3 +166,38 @@ def test_batch_wait_that_gives_up_reports_timeout_and_the_launch_ends(torch_cuda
             want = orc.mclahe(xh, s["kernel"], s["n_bins"], s["clip_limit"], mode=int(s["adaptive"]),
                               range_=s.get("global_range"))
             assert np.abs(out.cpu().numpy().astype(np.float64) - want).max() <= 1e-5, s
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("branches", [1, 3, 16])
+def test_concurrent_batch_equals_per_volume_forward(torch_cuda, orc, use_graph, branches):
+    """mclahe_batch_concurrent runs each volume's own forward pass on parallel
+    branches: every output equals mclahe_forward's with the same plan bit for bit
+    (the plans' own shapes and walks), call after call."""
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE, MCLAHEBatch
+
+    specs = _specs()
+    xs_h = _inputs(specs, 31)
+    xs = [torch.from_numpy(x).cuda() for x in xs_h]
+    batch = MCLAHEBatch(specs)
+    for rep in range(2):
+        outs = batch.forward(xs, outs=[torch.full_like(x, -1.0) for x in xs], use_graph=use_graph,
+                             concurrent=branches)
+        torch.cuda.synchronize()
+        for v, (x, xh, s, out) in enumerate(zip(xs, xs_h, specs, outs)):
+            op = MCLAHE(s["shape"], s["kernel"], s["n_bins"], s["clip_limit"], s["adaptive"],
+                        s.get("global_range"))
+            op.set_shapes(**batch_shapes(nat, batch.plans[v]))
+            assert torch.equal(out, op.forward(x)), (rep, s)
+            if rep == 0:
+                want = orc.mclahe(xh, s["kernel"], s["n_bins"], s["clip_limit"], mode=int(s["adaptive"]),
+                                  range_=s.get("global_range"))
+                assert np.abs(out.cpu().numpy().astype(np.float64) - want).max() <= 1e-5, s
+
+
+def batch_shapes(nat, plan):
+    i = nat.mclahe_plan_query(plan)
+    return {k: int(i[k]) for k in ("hist_group", "hist_cluster", "hist_copies", "hist_shares", "hist_walk",
+                                   "hist_threads", "map_chunks", "map_tma", "map_flat")}

@@ -46,7 +46,8 @@ def pass_kernel(pass_name, info):
     if pass_name == "range":
         return "k_hist_flat" if (flat and info["mode"] == 1) else "k_range_global"
     mapk = "k_map_tma" if info["map_tma"] else ("k_map_flat" if info["map_flat"] else "k_map")
-    return {"hist": "k_hist_flat" if flat else "k_hist", "map": mapk}[pass_name]
+    histk = "k_hist_flat" if flat else ("k_hist_staged" if info["hist_walk"] == 3 else "k_hist")
+    return {"hist": histk, "map": mapk}[pass_name]
 
 
 
@@ -189,7 +190,8 @@ def algorithmic_bytes(info, adaptive, has_range):
 def kernel_source_hash(pass_name):
     """Hash of the sources a pass's kernel is compiled from (the recorded ncu
     traffic is only reported while this matches)."""
-    hist = ("k_hist.cu", "k_hist_tma.cu", "k_hist_lsu.cu", "k_hist_impl.cuh", "hist_impl.cuh", "tma.cuh")
+    hist = ("k_hist.cu", "k_hist_tma.cu", "k_hist_lsu.cu", "k_hist_staged.cu", "k_hist_impl.cuh",
+            "hist_impl.cuh", "hist_staged.cuh", "tma.cuh")
     files = {"range": ("k_range.cu",) + hist, "hist": hist,
              "map": ("k_map.cu", "k_map_impl.cuh", "map_impl.cuh", "tma.cuh")}[pass_name]
     h = hashlib.sha256()
@@ -400,8 +402,10 @@ def measure_fwd_bwd(dev, steps, warmup):
     """Forward + backward of 8 volumes 64x256x256 (fluorescence-like; kernel
     16x64x64, 256 bins, adaptive range) with one learnable clip limit per
     volume (U[0.005, 0.05]) and loss = mean squared error to a seeded target;
-    against the forward alone."""
-    import numpy as np
+    against the forward alone.  The step is what MCLAHEBatchFunction runs: one
+    mclahe_forward_batch call (the eight forwards on parallel branches), dL/dout
+    of the loss (two elementwise launches over the batch), one
+    mclahe_backward_batch call; the per-volume calls are timed beside it."""
     import torch
 
     from paper_1906_11355_gb300 import _native as nat
@@ -409,53 +413,64 @@ def measure_fwd_bwd(dev, steps, warmup):
     from paper_1906_11355_gb300.api import MCLAHE
 
     B, shape, ks, nb = 8, (64, 256, 256), (16, 64, 64), 256
-    xs = [synth.fluorescence_t(shape, seed=2000 + v, device=dev) for v in range(B)]
-    tgt = [synth.fluorescence_t(shape, seed=3000 + v, device=dev) for v in range(B)]
-    tgt = [t / t.max() for t in tgt]
+    xs = torch.stack([synth.fluorescence_t(shape, seed=2000 + v, device=dev) for v in range(B)])
+    tgt = torch.stack([synth.fluorescence_t(shape, seed=3000 + v, device=dev) for v in range(B)])
+    tgt /= tgt.amax(dim=(1, 2, 3), keepdim=True)
     g = torch.Generator(device="cpu")
     g.manual_seed(4)
     clips = (0.005 + 0.045 * torch.rand(B, generator=g)).to(dev)
     op = MCLAHE(shape, ks, nb, 0.02, adaptive=True, device=dev)
     wss = [torch.zeros(op.ws_bytes, dtype=torch.uint8, device=dev) for _ in range(B)]
-    outs = [torch.empty_like(x) for x in xs]
-    gouts = [torch.empty_like(x) for x in xs]
+    outs = torch.empty_like(xs)
+    gouts = torch.empty_like(xs)
     gclip = torch.empty(B, dtype=torch.float32, device=dev)
-    n = float(B * xs[0].numel())
+    n = float(xs.numel())
     stream = torch.cuda.current_stream(dev)
+    xl, ol, gl = list(xs), list(outs), list(gouts)
 
     def fwd():
-        for v in range(B):
-            nat.mclahe_forward(op.plan, xs[v], outs[v], wss[v], op.ws_bytes, clips[v:v + 1], stream)
+        nat.mclahe_forward_batch(op.plan, xl, ol, wss, op.ws_bytes, clips, stream)
+
+    def bwd():
+        nat.mclahe_backward_batch(op.plan, xl, gl, wss, op.ws_bytes, clips, gclip, stream)
 
     def fwd_bwd():
         fwd()
-        for v in range(B):
-            torch.sub(outs[v], tgt[v], out=gouts[v]).mul_(2.0 / n)   # dL/d(out) of the MSE
-            nat.mclahe_backward(op.plan, xs[v], gouts[v], wss[v], op.ws_bytes, clips[v:v + 1], None,
-                                gclip[v:v + 1], stream)
+        torch.sub(outs, tgt, out=gouts).mul_(2.0 / n)   # dL/d(out) of the MSE
+        bwd()
 
-    def bwd():   # the backward calls alone (upstream gradients already in gouts)
+    def fwd_pv():
         for v in range(B):
-            nat.mclahe_backward(op.plan, xs[v], gouts[v], wss[v], op.ws_bytes, clips[v:v + 1], None,
+            nat.mclahe_forward(op.plan, xl[v], ol[v], wss[v], op.ws_bytes, clips[v:v + 1], stream)
+
+    def bwd_pv():
+        for v in range(B):
+            nat.mclahe_backward(op.plan, xl[v], gl[v], wss[v], op.ws_bytes, clips[v:v + 1], None,
                                 gclip[v:v + 1], stream)
 
     ms_fwd = _time_steps(fwd, steps, warmup, stream)
     ms_fb = _time_steps(fwd_bwd, steps, warmup, stream)
     ms_bwd = _time_steps(bwd, steps, warmup, stream)
+    ms_fwd_pv = _time_steps(fwd_pv, steps, warmup, stream)
+    ms_bwd_pv = _time_steps(bwd_pv, steps, warmup, stream)
     voxels = int(n)
     peak, peak_kind = measured_peak_gbs()
     bwd_bytes = 8 * voxels   # reads of the input and the upstream gradient
+
+    def roof(ms):
+        ach = bwd_bytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "algorithmic_bytes": bwd_bytes, "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind}
+
     out = {"workload": "fwd+bwd-8x64x256x256-learnable-clip", "voxels": voxels,
            "value": voxels / (ms_fb * 1e-3) / 1e9, "unit": "Gvoxel/s", "ms_per_step": ms_fb,
            "forward_ms": ms_fwd, "forward_value": voxels / (ms_fwd * 1e-3) / 1e9,
            "fwd_bwd_over_fwd": ms_fb / ms_fwd,
            "backward_ms": ms_bwd,
-           "backward_roofline": {"bound": "hbm", "algorithmic_bytes": bwd_bytes,
-                                 "achieved": bwd_bytes / (ms_bwd * 1e-3) / 1e9, "peak": peak,
-                                 "unit": "GB/s", "frac": bwd_bytes / (ms_bwd * 1e-3) / 1e9 / peak,
-                                 "peak_kind": peak_kind,
-                                 "note": "8 mclahe_backward calls (k_gmax, k_adj, k_lutbwd, "
-                                         "k_clipgrad each), 8 B per voxel"},
+           "backward_roofline": dict(roof(ms_bwd), note="one mclahe_backward_batch call (k_dtab, "
+                                     "k_mapdot, k_clipsum over the 8 volumes), 8 B per voxel"),
+           "per_volume_calls": {"forward_ms": ms_fwd_pv, "backward_ms": ms_bwd_pv,
+                                "backward_frac": roof(ms_bwd_pv)["frac"]},
            "grad_clip_finite": bool(torch.isfinite(gclip).all().item()),
            "data": "synthetic, drawn on the device (torch generators, seeds 2000+v, targets 3000+v)"}
     del xs, tgt, wss, outs, gouts

@@ -333,13 +333,57 @@ MCLAHE_API mclahe_status mclahe_forward_slab(mclahe_plan_t plan, mclahe_pass pas
  *   d_clip        the same clip pointer as the forward call (nullable).
  *   d_grad_lut    nullable device float [K][n_bins]: receives dL/dlut.
  *   d_grad_clip   device float scalar: receives dL/dclip_limit.
- * The per-voxel terms g_v * c_i(v) are summed as fixed-point integers (each
- * rounded at a scale set by max |g|, relative resolution 2^-30 of it), so the
- * results are deterministic; the plan requires kernel_size[D-1] <= 65535.
+ * With d_grad_lut given, the per-voxel terms g_v * c_i(v) are summed as
+ * fixed-point integers (each rounded at a scale set by max |g|, relative
+ * resolution 2^-30 of it); the plan requires kernel_size[D-1] <= 65535.  With
+ * d_grad_lut NULL only dL/dclip is formed, as a gather: the tables
+ * d lut_kj / dT interpolated like the mapping pass and dotted with g
+ * (compensated fp32 per thread, then double in a fixed order).  Both forms are
+ * deterministic for a given plan.
  */
 MCLAHE_API mclahe_status mclahe_backward(mclahe_plan_t plan, const float *d_in, const float *d_grad_out,
                               void *d_ws, size_t ws_bytes, const float *d_clip, float *d_grad_lut,
                               float *d_grad_clip, mclahe_stream_t stream);
+
+/*
+ * mclahe_forward_batch -- mclahe_forward on n_vol volumes of one plan, each
+ * with its own workspace (which then serves mclahe_backward or
+ * mclahe_backward_batch), on `branches` (1..16) parallel branches forked from
+ * `stream` and joined back into it, volumes dealt longest first to the least
+ * loaded branch, so the passes of small volumes overlap.  Each output equals
+ * mclahe_forward's bit for bit.  Nothing is cached between calls (the
+ * pointers may change every call).  No counterpart in the paper.
+ *   d_in, d_out, d_ws   host arrays of n_vol device pointers (outputs and
+ *                 workspaces pairwise distinct, no output another volume's
+ *                 input; workspaces of ws_bytes each).
+ *   d_clip        nullable device float [n_vol] clip limits (NULL: the plan's).
+ * Argument errors return before any launch.  The library's branch streams are
+ * shared by the process: concurrent calls from several host threads are
+ * serialised on the host.
+ */
+MCLAHE_API mclahe_status mclahe_forward_batch(mclahe_plan_t plan, int n_vol, const float *const *d_in,
+                                              float *const *d_out, void *const *d_ws, size_t ws_bytes,
+                                              const float *d_clip, mclahe_stream_t stream, int branches);
+
+/*
+ * mclahe_backward_batch -- dL/dclip_limit of n_vol forward calls of one plan
+ * (the gather form of mclahe_backward, d_grad_lut NULL), in three launches
+ * per 32 volumes instead of three per volume, so a batch of small volumes
+ * fills the GPU.  Volume v's result equals mclahe_backward's for it bit for
+ * bit.  No counterpart in the paper.
+ *   d_in, d_grad_out, d_ws   host arrays of n_vol device pointers: each
+ *                 volume's input, upstream gradient and the workspace of its
+ *                 forward call (ws_bytes each, pairwise distinct).
+ *   d_clip        nullable device float [n_vol]: the clip limits the forward
+ *                 calls read (NULL: the plan's).
+ *   d_grad_clip   device float [n_vol]: receives dL/dclip_limit per volume.
+ * Argument errors (a null or misaligned pointer, a small workspace, a shared
+ * workspace) return before any launch.
+ */
+MCLAHE_API mclahe_status mclahe_backward_batch(mclahe_plan_t plan, int n_vol, const float *const *d_in,
+                                               const float *const *d_grad_out, void *const *d_ws,
+                                               size_t ws_bytes, const float *d_clip,
+                                               float *d_grad_clip, mclahe_stream_t stream);
 
 /*
  * mclahe_batch -- Algorithm 1 on n_vol independent volumes of possibly

@@ -30,7 +30,8 @@ MCLAHE_RANGE_ADAPTIVE = 1
 # every symbol include/mclahe.h declares
 EXPORTS = (
     "mclahe_plan", "mclahe_plan_destroy", "mclahe_plan_query", "mclahe_workspace_bytes",
-    "mclahe_forward", "mclahe_backward", "mclahe_batch", "mclahe_batch_workspace_bytes",
+    "mclahe_forward", "mclahe_backward", "mclahe_backward_batch", "mclahe_forward_batch",
+    "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
     "mclahe_plan_set_shapes", "mclahe_forward_graph", "mclahe_noalloc_sync_status",
@@ -115,6 +116,10 @@ def load(path: str = LIB_PATH):
         lib.mclahe_forward_graph.restype = ctypes.c_int
         lib.mclahe_backward.argtypes = [vp, vp, vp, vp, sz, vp, vp, vp, vp]
         lib.mclahe_backward.restype = ctypes.c_int
+        lib.mclahe_backward_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, sz, vp, vp, vp]
+        lib.mclahe_backward_batch.restype = ctypes.c_int
+        lib.mclahe_forward_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, sz, vp, vp, ctypes.c_int]
+        lib.mclahe_forward_batch.restype = ctypes.c_int
         lib.mclahe_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), vp, sz, vp, vp, ctypes.c_int]
         lib.mclahe_batch.restype = ctypes.c_int
@@ -375,6 +380,29 @@ def mclahe_backward(plan, d_in, d_grad_out, d_ws, ws_bytes, d_clip, d_grad_lut, 
 def _ptr_array(items):
     arr = (ctypes.c_void_p * len(items))(*[_ptr(x) for x in items])
     return arr
+
+
+def mclahe_forward_batch(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None, branches=8):
+    """mclahe_forward on len(d_in) volumes of one plan on parallel branches
+    (lists of tensors or pointers; d_clip: n_vol clip limits or None)."""
+    n = len(d_in)
+    if len(d_out) != n or len(d_ws) != n:
+        raise ValueError("d_in, d_out and d_ws must have the same length")
+    st = load().mclahe_forward_batch(plan.handle, n, _ptr_array(d_in), _ptr_array(d_out), _ptr_array(d_ws),
+                                     int(ws_bytes), _ptr(d_clip), _stream(stream), int(branches))
+    _check(st, "mclahe_forward_batch")
+
+
+def mclahe_backward_batch(plan, d_in, d_grad_out, d_ws, ws_bytes, d_clip, d_grad_clip, stream=None):
+    """dL/dclip of len(d_in) forward calls of one plan (lists of tensors or
+    pointers; d_clip: n_vol clip limits or None; d_grad_clip: n_vol floats)."""
+    n = len(d_in)
+    if len(d_grad_out) != n or len(d_ws) != n:
+        raise ValueError("d_in, d_grad_out and d_ws must have the same length")
+    st = load().mclahe_backward_batch(plan.handle, n, _ptr_array(d_in), _ptr_array(d_grad_out),
+                                      _ptr_array(d_ws), int(ws_bytes), _ptr(d_clip), _ptr(d_grad_clip),
+                                      _stream(stream))
+    _check(st, "mclahe_backward_batch")
 
 
 def mclahe_batch_workspace_bytes(plans) -> int:

@@ -45,6 +45,41 @@ class MCLAHEFunction(torch.autograd.Function):
         return gx, gc, None
 
 
+class MCLAHEBatchFunction(torch.autograd.Function):
+    """out[b] = MCLAHE(x[b]; clip[b]) for a batch x [B, *shape] of volumes of
+    one plan.  The forward pass is one mclahe_forward_batch call (every
+    volume's forward on parallel branches, each with its own workspace); the
+    backward pass is one mclahe_backward_batch call (three launches per 32
+    volumes)."""
+
+    @staticmethod
+    def forward(ctx, x, clip, op):
+        if x.dim() != len(op.shape) + 1 or tuple(x.shape[1:]) != tuple(op.shape):
+            raise ValueError("x must be [B, *shape] of the plan's shape")
+        x = x.contiguous()
+        clip = clip.reshape(-1).contiguous()
+        if clip.numel() != x.shape[0]:
+            raise ValueError("one clip limit per volume")
+        out = torch.empty_like(x)
+        ws = [torch.zeros(op.ws_bytes, dtype=torch.uint8, device=x.device) for _ in range(x.shape[0])]
+        nat.mclahe_forward_batch(op.plan, list(x), list(out), ws, op.ws_bytes, clip)
+        ctx.save_for_backward(x, clip)
+        ctx.ws = ws
+        ctx.op = op
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        x, clip = ctx.saved_tensors
+        op = ctx.op
+        g = grad_out.contiguous()
+        grad_clip = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        nat.mclahe_backward_batch(op.plan, [x[b] for b in range(x.shape[0])],
+                                  [g[b] for b in range(x.shape[0])], ctx.ws, op.ws_bytes, clip, grad_clip)
+        gx = torch.zeros_like(x) if ctx.needs_input_grad[0] else None
+        return gx, grad_clip if ctx.needs_input_grad[1] else None, None
+
+
 _ops = {}
 
 
@@ -69,6 +104,4 @@ def mclahe_autograd(x, clip, kernel_size, n_bins=256, adaptive=False, global_ran
     if x.dim() != nd + 1:
         raise ValueError("x must have len(kernel_size) or len(kernel_size) + 1 dimensions")
     op = _op(x.shape[1:], kernel_size, n_bins, adaptive, global_range, x.device)
-    clip = clip.reshape(-1)
-    outs = [MCLAHEFunction.apply(x[b].contiguous(), clip[b:b + 1], op) for b in range(x.shape[0])]
-    return torch.stack(outs)
+    return MCLAHEBatchFunction.apply(x, clip.reshape(-1), op)

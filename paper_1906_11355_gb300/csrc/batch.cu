@@ -273,15 +273,19 @@ BranchPool *branch_pool() {
     return &p;
 }
 
-// Every volume's own forward pass (its plan's launch shapes and walks) on one
-// of `branches` parallel branches forked from st and joined back into it;
-// volumes are dealt longest first to the least loaded branch.
-mclahe_status enqueue_concurrent(int n_vol, const mclahe_plan_t *plans, const float *const *d_in,
-                                 float *const *d_out, unsigned char *ws, const float *d_clip,
-                                 cudaStream_t st, int branches) {
+// Every volume's own forward pass (its plan's launch shapes and walks, its
+// own workspace ws[v]) on one of `branches` parallel branches forked from st
+// and joined back into it; volumes are dealt longest first to the least
+// loaded branch.  The pool's streams and events are shared by the process, so
+// one enqueue runs at a time.
+std::mutex g_enqueue_mutex;
+
+mclahe_status enqueue_concurrent_ws(int n_vol, const mclahe_plan_t *plans, const float *const *d_in,
+                                    float *const *d_out, unsigned char *const *ws, const float *d_clip,
+                                    cudaStream_t st, int branches) {
     BranchPool *pool = branch_pool();
     if (!pool) return MCLAHE_ERR_CUDA;
-    const BatchLayout L = batch_layout(n_vol, plans);
+    std::lock_guard<std::mutex> lock(g_enqueue_mutex);
     branches = std::max(1, std::min({branches, kMaxBranches, n_vol}));
     std::vector<int> order(n_vol);
     for (int v = 0; v < n_vol; ++v) order[v] = v;
@@ -299,7 +303,7 @@ mclahe_status enqueue_concurrent(int n_vol, const mclahe_plan_t *plans, const fl
         cudaStream_t sb = pool->s[b];
         if (cudaStreamWaitEvent(sb, pool->fork, 0) != cudaSuccess) return MCLAHE_ERR_CUDA;
         for (int v : lists[b]) {
-            const mclahe_status s = forward_impl(*plans[v], d_in[v], d_out[v], ws + L.vol[v],
+            const mclahe_status s = forward_impl(*plans[v], d_in[v], d_out[v], ws[v],
                                                  d_clip ? d_clip + v : nullptr, sb);
             if (s != MCLAHE_OK) return s;
         }
@@ -307,6 +311,15 @@ mclahe_status enqueue_concurrent(int n_vol, const mclahe_plan_t *plans, const fl
         if (cudaStreamWaitEvent(st, pool->join[b], 0) != cudaSuccess) return MCLAHE_ERR_CUDA;
     }
     return MCLAHE_OK;
+}
+
+mclahe_status enqueue_concurrent(int n_vol, const mclahe_plan_t *plans, const float *const *d_in,
+                                 float *const *d_out, unsigned char *ws, const float *d_clip,
+                                 cudaStream_t st, int branches) {
+    const BatchLayout L = batch_layout(n_vol, plans);
+    std::vector<unsigned char *> wsv(n_vol);
+    for (int v = 0; v < n_vol; ++v) wsv[v] = ws + L.vol[v];
+    return enqueue_concurrent_ws(n_vol, plans, d_in, d_out, wsv.data(), d_clip, st, branches);
 }
 
 }  // namespace
@@ -399,6 +412,27 @@ mclahe_status mclahe_batch_concurrent(int n_vol, const mclahe_plan_t *plans, con
     return replay_cached(key, st, [&](cudaStream_t cap) {
         return enqueue_concurrent(n_vol, plans, d_in, d_out, ws, d_clip, cap, branches);
     });
+}
+
+mclahe_status mclahe_forward_batch(mclahe_plan_t plan, int n_vol, const float *const *d_in,
+                                   float *const *d_out, void *const *d_ws, size_t ws_bytes,
+                                   const float *d_clip, mclahe_stream_t stream, int branches) {
+    if (!plan || n_vol < 0 || branches < 1 || (n_vol > 0 && (!d_in || !d_out || !d_ws)))
+        return MCLAHE_ERR_INVALID_ARG;
+    if (d_clip && (reinterpret_cast<uintptr_t>(d_clip) & 3)) return MCLAHE_ERR_INVALID_ARG;
+    for (int v = 0; v < n_vol; ++v) {
+        const mclahe_status s = check_forward_args(plan, d_in[v], d_out[v], d_ws[v], ws_bytes);
+        if (s != MCLAHE_OK) return s;
+        for (int u = 0; u < v; ++u)
+            if (d_ws[u] == d_ws[v] || d_out[u] == d_out[v] || d_out[u] == d_in[v] ||
+                d_in[u] == d_out[v])
+                return MCLAHE_ERR_INVALID_ARG;
+    }
+    if (n_vol == 0) return MCLAHE_OK;
+    std::vector<mclahe_plan_t> plans(n_vol, plan);
+    return enqueue_concurrent_ws(n_vol, plans.data(), d_in, d_out,
+                                 reinterpret_cast<unsigned char *const *>(d_ws), d_clip,
+                                 reinterpret_cast<cudaStream_t>(stream), branches);
 }
 
 mclahe_status mclahe_batch_set_wait(uint32_t max_polls, int unreachable) {

@@ -473,3 +473,32 @@ extern "C" mclahe_status mclahe_backward(mclahe_plan_t p, const float *d_in,
                                     d_grad_lut, d_grad_clip, reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? MCLAHE_OK : MCLAHE_ERR_CUDA;
 }
+
+namespace mclahe {
+// k_bwd_gather.cu: the gather form over n_vol volumes of one plan (host arrays
+// of device pointers; d_clip nullable, else n_vol clip limits; d_grad_clip
+// n_vol floats)
+cudaError_t launch_backward_gather_many(const mclahe_plan_s &p, int n_vol, const float *const *in,
+                                        const float *const *gout, void *const *ws,
+                                        const float *d_clip, float *d_grad_clip, cudaStream_t st);
+}  // namespace mclahe
+
+extern "C" mclahe_status mclahe_backward_batch(mclahe_plan_t p, int n_vol, const float *const *d_in,
+                                               const float *const *d_grad_out, void *const *d_ws,
+                                               size_t ws_bytes, const float *d_clip,
+                                               float *d_grad_clip, mclahe_stream_t stream) {
+    if (!p || n_vol < 0 || !d_grad_clip || (n_vol > 0 && (!d_in || !d_grad_out || !d_ws)))
+        return MCLAHE_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_grad_clip) & 3) return MCLAHE_ERR_INVALID_ARG;
+    if (d_clip && (reinterpret_cast<uintptr_t>(d_clip) & 3)) return MCLAHE_ERR_INVALID_ARG;
+    for (int v = 0; v < n_vol; ++v) {
+        const mclahe_status s = check_forward_args(p, d_in[v], d_grad_out[v], d_ws[v], ws_bytes);
+        if (s != MCLAHE_OK) return s;
+        for (int u = 0; u < v; ++u)
+            if (d_ws[u] == d_ws[v]) return MCLAHE_ERR_INVALID_ARG;
+    }
+    if (n_vol == 0) return MCLAHE_OK;
+    const cudaError_t e = launch_backward_gather_many(*p, n_vol, d_in, d_grad_out, d_ws, d_clip,
+                                                      d_grad_clip, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MCLAHE_OK : MCLAHE_ERR_CUDA;
+}

@@ -22,6 +22,8 @@
 //   k_clipsum   one CTA: the partials in a fixed order, times V (0 when the
 //               clip limit given lies outside [0, 1], where the forward
 //               clamps it).
+// Each launch covers up to 32 volumes of one plan (blockIdx.y), so a batch of
+// small volumes fills the GPU in three launches (mclahe_backward_batch).
 // No atomics: the result depends only on the launch shape (deterministic).
 #include <algorithm>
 
@@ -30,17 +32,34 @@
 
 namespace mclahe {
 
-__global__ void __launch_bounds__(256) k_dtab(Geom g, const uint32_t *__restrict__ hist,
-                                              const float *__restrict__ lut,
-                                              const float *__restrict__ d_clip,
-                                              float *__restrict__ dtab) {
+// The volumes of one launch (blockIdx.y): the same plan, each its own input,
+// upstream gradient, workspace and clip-limit slot.
+constexpr int kBwdVols = 32;
+struct BwdVols {
+    const float *in[kBwdVols];
+    const float *gout[kBwdVols];
+    unsigned char *ws[kBwdVols];
+    float *gclip[kBwdVols];
+};
+
+// Where the gather's scratch lies in a workspace.
+struct GatherLayout {
+    size_t hist, lut, lo, scale, dtab, partial;
+};
+
+__global__ void __launch_bounds__(256) k_dtab(Geom g, const __grid_constant__ BwdVols v, GatherLayout L,
+                                              const float *__restrict__ d_clip) {
     extern __shared__ __align__(16) uint32_t h[];   // nb counts
     __shared__ float s_last;
     const int nb = g.nb, LS = g.LS;
     const int64_t k = blockIdx.x;
+    unsigned char *ws = v.ws[blockIdx.y];
+    const uint32_t *hist = reinterpret_cast<const uint32_t *>(ws + L.hist);
+    const float *lut = reinterpret_cast<const float *>(ws + L.lut);
+    float *dtab = reinterpret_cast<float *>(ws + L.dtab);
     for (int j = threadIdx.x; j < nb; j += blockDim.x) h[j] = __ldcg(hist + k * nb + j);
     __syncthreads();
-    const LutStats st = lut_stats(h, nb, g.V, load_clip(d_clip, g.clip));
+    const LutStats st = lut_stats(h, nb, g.V, load_clip(d_clip ? d_clip + blockIdx.y : nullptr, g.clip));
     const float ncb = __fdiv_rn(float(st.N_c), float(nb));
     const float c2 = __fsub_rn(float(st.A0), ncb);
     int64_t Aj = st.pa;
@@ -76,28 +95,31 @@ __device__ __forceinline__ double block_sum_d(double v) {
 
 template <int D, bool ADAPTIVE, bool REPL>
 __global__ void __launch_bounds__(256, D >= 4 && ADAPTIVE ? 1 : 2)
-    k_mapdot(Geom g, const float *__restrict__ in, const float *__restrict__ gout,
-             const float *__restrict__ dtab, const float *__restrict__ lo_k,
-             const float *__restrict__ scale_k, int chunks, double *__restrict__ partial) {
+    k_mapdot(Geom g, const __grid_constant__ BwdVols v, GatherLayout L, int chunks) {
     extern __shared__ __align__(16) float tab[];
     const int64_t cell = blockIdx.x / chunks;
     const int chunk = int(blockIdx.x - cell * chunks);
+    const unsigned char *ws = v.ws[blockIdx.y];
     float2 kd;
-    map_cell<D, ADAPTIVE, REPL, kWalkLsu, true>(g, in, nullptr, dtab, lo_k, scale_k, cell, chunk,
-                                                chunks, tab, nullptr, -1, gout, &kd);
+    map_cell<D, ADAPTIVE, REPL, kWalkLsu, true>(
+        g, v.in[blockIdx.y], nullptr, reinterpret_cast<const float *>(ws + L.dtab),
+        reinterpret_cast<const float *>(ws + L.lo), reinterpret_cast<const float *>(ws + L.scale), cell,
+        chunk, chunks, tab, nullptr, -1, v.gout[blockIdx.y], &kd);
     const double s = block_sum_d(double(kd.x) - double(kd.y));
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0)
+        reinterpret_cast<double *>(v.ws[blockIdx.y] + L.partial)[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(256) k_clipsum(const double *__restrict__ partial, int n,
+__global__ void __launch_bounds__(256) k_clipsum(const __grid_constant__ BwdVols v, GatherLayout L, int n,
                                                  int64_t V, const float *__restrict__ d_clip,
-                                                 float plan_clip, float *__restrict__ out) {
+                                                 float plan_clip) {
+    const double *partial = reinterpret_cast<const double *>(v.ws[blockIdx.x] + L.partial);
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
     s = block_sum_d(s);
     if (threadIdx.x == 0) {
-        const float raw = d_clip ? *d_clip : plan_clip;
-        out[0] = (raw >= 0.0f && raw <= 1.0f) ? float(double(V) * s) : 0.0f;
+        const float raw = d_clip ? d_clip[blockIdx.x] : plan_clip;
+        v.gclip[blockIdx.x][0] = (raw >= 0.0f && raw <= 1.0f) ? float(double(V) * s) : 0.0f;
     }
 }
 
@@ -107,31 +129,37 @@ size_t bwd_gather_bytes(const Geom &g, int chunks) {
     return tab + sizeof(double) * size_t(n_cells(g)) * size_t(chunks);
 }
 
+static GatherLayout gather_layout(const mclahe_plan_s &p) {
+    GatherLayout L;
+    L.hist = p.ws.hist;
+    L.lut = p.ws.lut;
+    L.lo = p.ws.lo;
+    L.scale = p.ws.scale;
+    L.dtab = p.ws.scratch;
+    L.partial = p.ws.scratch + ((sizeof(float) * size_t(p.g.K) * p.g.LS + 255) & ~size_t(255));
+    return L;
+}
+
+// One launch of each kernel over nv (<= kBwdVols) volumes; d_clip (nullable)
+// points at the first of their clip limits.
 template <int D>
-static cudaError_t launch_gather_d(const mclahe_plan_s &p, const float *in, const float *gout,
-                                   unsigned char *ws, const float *d_clip, float *d_grad_clip,
-                                   cudaStream_t st) {
+static cudaError_t launch_gather_d(const mclahe_plan_s &p, const BwdVols &v, int nv,
+                                   const float *d_clip, cudaStream_t st) {
     const Geom &g = p.g;
     const int chunks = p.t.bwd_chunks;
-    float *dtab = reinterpret_cast<float *>(ws + p.ws.scratch);
-    double *partial = reinterpret_cast<double *>(
-        ws + p.ws.scratch + ((sizeof(float) * size_t(g.K) * g.LS + 255) & ~size_t(255)));
+    const GatherLayout L = gather_layout(p);
     const size_t smem_h = sizeof(uint32_t) * size_t(g.nb);
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_dtab), smem_h);
     if (e != cudaSuccess) return e;
-    k_dtab<<<unsigned(g.K), 256, smem_h, st>>>(g, reinterpret_cast<const uint32_t *>(ws + p.ws.hist),
-                                               reinterpret_cast<const float *>(ws + p.ws.lut), d_clip,
-                                               dtab);
+    k_dtab<<<dim3(unsigned(g.K), unsigned(nv)), 256, smem_h, st>>>(g, v, L, d_clip);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned grid = unsigned(n_cells(g) * chunks);
     const size_t smem = map_smem_for(D, g.P, false);
-    const float *lo = reinterpret_cast<const float *>(ws + p.ws.lo);
-    const float *sc = reinterpret_cast<const float *>(ws + p.ws.scale);
     const bool a = g.mode == MCLAHE_RANGE_ADAPTIVE, repl = map_repl_fits(g.P);
 #define MCLAHE_DOT(A, R)                                                                    \
     e = ensure_smem(reinterpret_cast<const void *>(k_mapdot<D, A, R>), smem);              \
     if (e != cudaSuccess) return e;                                                         \
-    k_mapdot<D, A, R><<<grid, 256, smem, st>>>(g, in, gout, dtab, lo, sc, chunks, partial);
+    k_mapdot<D, A, R><<<dim3(grid, unsigned(nv)), 256, smem, st>>>(g, v, L, chunks);
     if (a) {
         if (repl) { MCLAHE_DOT(true, true) } else { MCLAHE_DOT(true, false) }
     } else {
@@ -139,20 +167,48 @@ static cudaError_t launch_gather_d(const mclahe_plan_s &p, const float *in, cons
     }
 #undef MCLAHE_DOT
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_clipsum<<<1, 256, 0, st>>>(partial, int(grid), g.V, d_clip, g.clip, d_grad_clip);
+    k_clipsum<<<unsigned(nv), 256, 0, st>>>(v, L, int(grid), g.V, d_clip, g.clip);
     return cudaGetLastError();
+}
+
+static cudaError_t launch_gather(const mclahe_plan_s &p, const BwdVols &v, int nv, const float *d_clip,
+                                 cudaStream_t st) {
+    switch (p.g.D) {
+        case 1: return launch_gather_d<1>(p, v, nv, d_clip, st);
+        case 2: return launch_gather_d<2>(p, v, nv, d_clip, st);
+        case 3: return launch_gather_d<3>(p, v, nv, d_clip, st);
+        case 4: return launch_gather_d<4>(p, v, nv, d_clip, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_backward_gather(const mclahe_plan_s &p, const float *in, const float *gout,
                                    unsigned char *ws, const float *d_clip, float *d_grad_clip,
                                    cudaStream_t st) {
-    switch (p.g.D) {
-        case 1: return launch_gather_d<1>(p, in, gout, ws, d_clip, d_grad_clip, st);
-        case 2: return launch_gather_d<2>(p, in, gout, ws, d_clip, d_grad_clip, st);
-        case 3: return launch_gather_d<3>(p, in, gout, ws, d_clip, d_grad_clip, st);
-        case 4: return launch_gather_d<4>(p, in, gout, ws, d_clip, d_grad_clip, st);
-        default: return cudaErrorInvalidValue;
+    BwdVols v{};
+    v.in[0] = in;
+    v.gout[0] = gout;
+    v.ws[0] = ws;
+    v.gclip[0] = d_grad_clip;
+    return launch_gather(p, v, 1, d_clip, st);
+}
+
+cudaError_t launch_backward_gather_many(const mclahe_plan_s &p, int n_vol, const float *const *in,
+                                        const float *const *gout, void *const *ws,
+                                        const float *d_clip, float *d_grad_clip, cudaStream_t st) {
+    for (int v0 = 0; v0 < n_vol; v0 += kBwdVols) {
+        const int nv = std::min(kBwdVols, n_vol - v0);
+        BwdVols v{};
+        for (int i = 0; i < nv; ++i) {
+            v.in[i] = in[v0 + i];
+            v.gout[i] = gout[v0 + i];
+            v.ws[i] = static_cast<unsigned char *>(ws[v0 + i]);
+            v.gclip[i] = d_grad_clip + v0 + i;
+        }
+        const cudaError_t e = launch_gather(p, v, nv, d_clip ? d_clip + v0 : nullptr, st);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 }  // namespace mclahe

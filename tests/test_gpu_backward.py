@@ -226,3 +226,60 @@ def test_clip_gradient_alone_gather_matches_oracle_and_scatter(torch_cuda, orc, 
     nat.mclahe_backward(op.plan, xd, gd, op.ws, op.ws_bytes, out_clip, None, gc)
     torch.cuda.synchronize()
     assert gc.item() == 0.0
+
+
+@pytest.mark.parametrize("n_vol,adaptive", [(35, True), (5, False)])
+def test_backward_batch_equals_per_volume_backward(torch_cuda, orc, n_vol, adaptive):
+    """mclahe_backward_batch (three launches per 32 volumes, here two groups
+    with 35 volumes) gives every volume the clip gradient mclahe_backward gives
+    it, bit for bit, with per-volume clip limits on the device (one outside
+    [0, 1]: zero gradient); a few checked against the oracle."""
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    shape, ks, nb = (12, 20, 28), (4, 8, 7), 64
+    rng = np.random.default_rng(71 + n_vol)
+    xs = [rng.gamma(2.0, size=shape).astype(np.float32) for _ in range(n_vol)]
+    gs = [rng.normal(size=shape).astype(np.float32) for _ in range(n_vol)]
+    clips = (0.005 + 0.05 * rng.random(n_vol)).astype(np.float32)
+    clips[3] = 1.25
+    op = MCLAHE(shape, ks, n_bins=nb, clip_limit=0.02, adaptive=adaptive)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    gd = [torch.from_numpy(g).cuda() for g in gs]
+    cd = torch.from_numpy(clips).cuda()
+    ws = [torch.zeros(op.ws_bytes, dtype=torch.uint8, device="cuda") for _ in range(n_vol)]
+    out = torch.empty(shape, device="cuda")
+    for v in range(n_vol):
+        nat.mclahe_forward(op.plan, xd[v], out, ws[v], op.ws_bytes, cd[v:v + 1])
+    got = torch.full((n_vol,), float("nan"), device="cuda")
+    nat.mclahe_backward_batch(op.plan, xd, gd, ws, op.ws_bytes, cd, got)
+    one = torch.empty(n_vol, device="cuda")
+    for v in range(n_vol):
+        nat.mclahe_backward(op.plan, xd[v], gd[v], ws[v], op.ws_bytes, cd[v:v + 1], None, one[v:v + 1])
+    torch.cuda.synchronize()
+    assert torch.equal(got, one)
+    assert got[3].item() == 0.0
+    for v in (0, n_vol - 1):
+        _, want = orc.mclahe_backward(xs[v], ks, nb, float(clips[v]), gs[v].astype(np.float64),
+                                      mode=int(adaptive))
+        want_lut, _ = orc.mclahe_backward(xs[v], ks, nb, float(clips[v]), gs[v].astype(np.float64),
+                                          mode=int(adaptive))
+        tol = REL * max(abs(want), 1e-3 * np.abs(want_lut).max())
+        assert abs(got[v].item() - want) <= tol, (v, got[v].item(), want)
+
+
+def test_backward_batch_rejects_bad_arguments(torch_cuda):
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    op = MCLAHE((16, 16), (4, 4), n_bins=32, clip_limit=0.02)
+    x = [torch.zeros((16, 16), device="cuda") for _ in range(2)]
+    ws = torch.zeros(op.ws_bytes, dtype=torch.uint8, device="cuda")
+    gc = torch.zeros(2, device="cuda")
+    with pytest.raises(nat.MclaheError):   # one workspace for two volumes
+        nat.mclahe_backward_batch(op.plan, x, x[::-1], [ws, ws], op.ws_bytes, None, gc)
+    with pytest.raises(nat.MclaheError):   # no output
+        nat.mclahe_backward_batch(op.plan, x, x[::-1], [ws, ws], op.ws_bytes, None, None)
+    nat.mclahe_backward_batch(op.plan, [], [], [], op.ws_bytes, None, gc)   # nothing to do

@@ -201,3 +201,61 @@ def batch_shapes(nat, plan):
     i = nat.mclahe_plan_query(plan)
     return {k: int(i[k]) for k in ("hist_group", "hist_cluster", "hist_copies", "hist_shares", "hist_walk",
                                    "hist_threads", "map_chunks", "map_tma", "map_flat")}
+
+
+@pytest.mark.parametrize("branches", [1, 4, 16])
+def test_forward_batch_of_one_plan_equals_forward(torch_cuda, orc, branches):
+    """mclahe_forward_batch: volumes of one plan, each with its own workspace,
+    on parallel branches: outputs, histograms and tables equal mclahe_forward's
+    bit for bit (per-volume clip limits on the device), and the workspaces
+    serve the batched backward."""
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    shape, ks, nb, n = (24, 40, 36), (6, 8, 9), 128, 11
+    rng = np.random.default_rng(90 + branches)
+    xs = torch.from_numpy(rng.gamma(2.0, size=(n,) + shape).astype(np.float32)).cuda()
+    clips = torch.from_numpy((0.01 + 0.04 * rng.random(n)).astype(np.float32)).cuda()
+    op = MCLAHE(shape, ks, n_bins=nb, clip_limit=0.02, adaptive=True)
+    ws = [torch.zeros(op.ws_bytes, dtype=torch.uint8, device="cuda") for _ in range(n)]
+    out = torch.full_like(xs, -1.0)
+    nat.mclahe_forward_batch(op.plan, list(xs), list(out), ws, op.ws_bytes, clips, None, branches)
+    one_ws = torch.zeros(op.ws_bytes, dtype=torch.uint8, device="cuda")
+    one = torch.empty(shape, device="cuda")
+    info = nat.mclahe_plan_query(op.plan)
+    for v in range(n):
+        nat.mclahe_forward(op.plan, xs[v], one, one_ws, op.ws_bytes, clips[v:v + 1])
+        torch.cuda.synchronize()
+        assert torch.equal(out[v], one), v
+        a, b = info["ws_hist"], info["ws_scratch"]   # histograms, ranges and tables
+        assert torch.equal(ws[v][a:b], one_ws[a:b]), v
+    want = orc.mclahe(xs[n - 1].cpu().numpy(), ks, nb, float(clips[n - 1].item()), mode=1)
+    assert np.abs(out[n - 1].cpu().numpy() - want).max() <= 1e-5
+    g = torch.from_numpy(rng.normal(size=(n,) + shape).astype(np.float32)).cuda()
+    gc = torch.empty(n, device="cuda")
+    nat.mclahe_backward_batch(op.plan, list(xs), list(g), ws, op.ws_bytes, clips, gc)
+    gc1 = torch.empty(1, device="cuda")
+    nat.mclahe_backward(op.plan, xs[3], g[3], ws[3], op.ws_bytes, clips[3:4], None, gc1)
+    torch.cuda.synchronize()
+    assert gc[3].item() == gc1.item()
+
+
+def test_forward_batch_rejects_bad_arguments(torch_cuda):
+    torch = torch_cuda
+    from paper_1906_11355_gb300 import _native as nat
+    from paper_1906_11355_gb300.api import MCLAHE
+
+    op = MCLAHE((16, 16), (4, 4), n_bins=32, clip_limit=0.02)
+    x = torch.zeros((2, 16, 16), device="cuda")
+    o = torch.zeros((2, 16, 16), device="cuda")
+    ws = [torch.zeros(op.ws_bytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    with pytest.raises(nat.MclaheError):   # one workspace for two volumes
+        nat.mclahe_forward_batch(op.plan, list(x), list(o), [ws[0], ws[0]], op.ws_bytes)
+    with pytest.raises(nat.MclaheError):   # one output for two volumes
+        nat.mclahe_forward_batch(op.plan, list(x), [o[0], o[0]], ws, op.ws_bytes)
+    with pytest.raises(nat.MclaheError):   # an output that is another volume's input
+        nat.mclahe_forward_batch(op.plan, list(x), [o[0], x[0]], ws, op.ws_bytes)
+    with pytest.raises(nat.MclaheError):
+        nat.mclahe_forward_batch(op.plan, list(x), list(o), ws, op.ws_bytes, branches=0)
+    nat.mclahe_forward_batch(op.plan, [], [], [], op.ws_bytes)   # nothing to do

@@ -143,3 +143,54 @@ def test_one_volume_split_across_gloo_ranks(world):
     want_hi = 0x7000_0000 + world - 1
     for r in res:
         assert r[3][0] == want_hi and r[3][1] == -1   # unsigned max of 0xffffffff - rank
+
+
+def _failing_worker(rank, world, port, q):
+    """Rank 1 fails on the host before the split-volume range exchange (an
+    exception between steps, none of its work in flight); rank 0 must get an
+    error from its next collective instead of waiting for ever."""
+    import datetime
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1906_11355_gb300 import dist as md
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    dist.barrier()
+    if rank == 1:
+        q.put((rank, "failed"))
+        q.close()
+        q.join_thread()
+        os._exit(3)   # the rank dies on the host
+    try:
+        md.combine_keys(torch.tensor([1, 2], dtype=torch.int32))
+        q.put((rank, "no error"))
+    except Exception as e:   # the peer's loss surfaces as an error of the collective
+        q.put((rank, "error: " + type(e).__name__))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_a_failed_rank_surfaces_as_an_error_on_the_others():
+    import time
+
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1] == "failed" and procs[1].exitcode == 3
+    assert res[0].startswith("error"), res[0]
+    assert procs[0].exitcode == 0
+    assert time.time() - t0 < 100

@@ -29,6 +29,9 @@ def test_gaussian_closed_forms():
     x = np.zeros(41)
     x[20] = 1.0
     assert np.abs(of.gaussian(x, (1.3,))[15:26] - w).max() < 1e-15
+    # symmetric normalised weights keep a linear ramp where no tap reaches a border
+    ramp = 0.5 + 0.25 * np.arange(40.0)
+    assert np.abs(of.gaussian(ramp, (1.3,))[r:-r] - ramp[r:-r]).max() < 1e-12
 
 
 def test_median_matches_scipy():

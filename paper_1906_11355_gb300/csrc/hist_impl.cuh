@@ -236,6 +236,7 @@ __device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int6
     const int per = (nb + 31) >> 5;
     const int j0 = min(lane * per, nb), j1 = min(j0 + per, nb);
     uint32_t nc = 0, su = 0;
+#pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         const uint32_t v = h[j];
         if (int64_t(v) > st.tf) nc += 1; else su += v;
@@ -262,6 +263,8 @@ __device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int6
     st.flat = (st.N_c == 0) && (st.S_tot == st.S0);
     st.den = st.diff(st.S_tot, st.N_c, nb - 1);
     int64_t Sj = is - su, Aj = ia - nc;   // exclusive prefixes at j0
+    // unrolled: the bins' divisions are independent and overlap
+#pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         const uint32_t v = h[j];
         if (int64_t(v) > st.tf) Aj += 1; else Sj += v;
@@ -271,7 +274,9 @@ __device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int6
 }
 
 // Tables of n kernels whose histograms lie in shared memory at h + i * P:
-// one block-wide build for a single kernel, else one warp per kernel.
+// one block-wide build for a single kernel, else one warp per kernel (block
+// builds one kernel after another measured slower on the 4-D workload: 3
+// kernels per 512-thread CTA).
 __device__ __forceinline__ void build_luts(const uint32_t *h, int P, int n, int nb, int LS, int64_t V,
                                            float clip, float *__restrict__ lut, int64_t k0,
                                            int64_t kstep) {
@@ -407,17 +412,19 @@ __device__ __forceinline__ void merge_and_build(const Geom &g, uint32_t *sh, uin
     if (C > 1) cluster.sync(); else __syncthreads();   // the other CTAs' shared memory is no longer read
 }
 
-// Phase 3: sum the R lane copies of every bin of GK kernels (copy (c + j) mod
-// R of bin j at step c: the threads of a warp read different banks) into
-// cnt[GK][P] and fold the padded indices >= n_bins - 1 into the last bin.
-// All threads of the block call it after the sweep's barrier.
+// Phase 3: sum the R lane copies of every bin of GK kernels into cnt[GK][P]
+// and fold the padded indices >= n_bins - 1 into the last bin.  Thread t sums
+// bin row t (words t R .. t R + R - 1); at step c lane l reads copy
+// (c + l R / 32) mod R, so the R lanes whose rows start in the same bank
+// (l mod 32/R equal, R <= 32) read R different banks: no conflicts.  All
+// threads of the block call it after the sweep's barrier.
 __device__ __forceinline__ void sum_copies(const uint32_t *sh, uint32_t *cnt, int GK, int P, int R,
                                            int nb) {
+    const int rot = (int(threadIdx.x & 31) * R) >> 5;
     for (int t = threadIdx.x; t < GK * P; t += blockDim.x) {
-        const int j = t % P;
         const uint32_t *row = sh + size_t(t) * R;
         uint32_t s = 0;
-        for (int c = 0; c < R; ++c) s += row[(c + j) & (R - 1)];
+        for (int c = 0; c < R; ++c) s += row[(c + rot) & (R - 1)];
         cnt[t] = s;
     }
     __syncthreads();

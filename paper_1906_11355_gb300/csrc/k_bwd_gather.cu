@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256, D >= 4 && ADAPTIVE ? 1 : 2)
     const int chunk = int(blockIdx.x - cell * chunks);
     const unsigned char *ws = v.ws[blockIdx.y];
     float2 kd;
-    map_cell<D, ADAPTIVE, REPL, kWalkLsu, true>(
+    map_cell<D, ADAPTIVE, REPL, D >= 3 ? kWalkRing : kWalkLsu, true>(
         g, v.in[blockIdx.y], nullptr, reinterpret_cast<const float *>(ws + L.dtab),
         reinterpret_cast<const float *>(ws + L.lo), reinterpret_cast<const float *>(ws + L.scale), cell,
         chunk, chunks, tab, nullptr, -1, v.gout[blockIdx.y], &kd);
@@ -154,7 +154,7 @@ static cudaError_t launch_gather_d(const mclahe_plan_s &p, const BwdVols &v, int
     k_dtab<<<dim3(unsigned(g.K), unsigned(nv)), 256, smem_h, st>>>(g, v, L, d_clip);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const unsigned grid = unsigned(n_cells(g) * chunks);
-    const size_t smem = map_smem_for(D, g.P, false);
+    const size_t smem = dot_smem_for(D, g.P);
     const bool a = g.mode == MCLAHE_RANGE_ADAPTIVE, repl = map_repl_fits(g.P);
 #define MCLAHE_DOT(A, R)                                                                    \
     e = ensure_smem(reinterpret_cast<const void *>(k_mapdot<D, A, R>), smem);              \

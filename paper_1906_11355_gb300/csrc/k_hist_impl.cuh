@@ -38,7 +38,12 @@ __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistT
            uint32_t *status, int64_t item0) {
     extern __shared__ __align__(128) uint32_t sh[];
     __shared__ __align__(8) uint64_t s_tbar[kHistTmaStages];
-    const int64_t item = item0 + blockIdx.x / cg::this_cluster().num_blocks();
+    // items in reverse launch order: the first clusters take the volume's end,
+    // which the preceding pass (range sweep, or the previous step's mapping)
+    // touched last and may still hold in L2; the mapping pass that follows
+    // starts at the volume's beginning, which this pass touches last
+    const unsigned ncl = cg::this_cluster().num_blocks();
+    const int64_t item = item0 + (gridDim.x / ncl - 1 - blockIdx.x / ncl);
     TmaRing<kHistTmaStages> tr{};
     if constexpr (HW == kHistTma)
         tr = tma_ring_init<kHistTmaStages>(s_tbar, hist_tma_stage0(sh, hist_smem_words(g.P, R, G)),

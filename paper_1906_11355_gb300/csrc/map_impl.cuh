@@ -96,6 +96,13 @@ __host__ __device__ inline size_t map_ring_bytes(int D) {
 __host__ __device__ inline size_t map_smem_for(int D, int P, bool ring = true) {
     return ((map_table_bytes(D, P) + 15) & ~size_t(15)) + (ring ? map_ring_bytes(D) : 0);
 }
+// The DOT form of 3- and 4-D cells streams the volume and the upstream
+// gradient through two rings of kDotStages row stages each.
+constexpr int kDotStages = 2;
+__host__ __device__ inline size_t dot_smem_for(int D, int P) {
+    return ((map_table_bytes(D, P) + 15) & ~size_t(15)) +
+           (D >= 3 ? 2 * size_t(kDotStages) * 4 * 256 * 16 : 0);
+}
 
 __device__ __forceinline__ void sts128(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
@@ -454,8 +461,16 @@ __device__ __forceinline__ void map_cell(const Geom &g, const T *__restrict__ in
                     if (sd.e0 + e >= 0 && sd.e0 + e < L) t = fmaf(gs[e], res[e], t);
                 kadd(t);
             };
-            walk_tile<D, QM, 4, MRow, DSlot, true>(in, gout, stride, box_lo, len, r0, r1, ts, true, slot,
-                                                   row2, quad);
+            if constexpr (RING && D >= 3 && std::is_same<T, float>::value) {
+                // x and g stream through two cp.async rings behind the tables
+                float4 *ring = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(tab) +
+                                                          ((map_table_bytes(D, P) + 15) & ~size_t(15)));
+                walk_tile_async<D, QM, kDotStages, MRow, DSlot, false, true>(
+                    in, stride, box_lo, len, r0, r1, ts, ring, slot, row2, quad, gout);
+            } else {
+                walk_tile<D, QM, 4, MRow, DSlot, true>(in, gout, stride, box_lo, len, r0, r1, ts, true,
+                                                       slot, row2, quad);
+            }
         } else {
             auto quad_fn = [&](MRow &st, const QuadRef &q) {
                 if (!q.has) return;

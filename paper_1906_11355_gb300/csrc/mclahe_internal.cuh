@@ -722,12 +722,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // FULL: the caller has checked that every slot of every row is a whole quad
 // inside the box (head 0, L = 4 * LPR * QMAX): no per-slot tests.
-template <int D, int QMAX, int ST, typename S, typename SD, bool FULL = false, typename T,
-          typename SlotFn, typename RowFn, typename QuadFn>
+// TWO: a second float32 volume in2 of the same layout streams through a second
+// ring right behind the first (ring + ST * QMAX * blockDim float4); quad_fn
+// gets its quad as the second value.
+template <int D, int QMAX, int ST, typename S, typename SD, bool FULL = false, bool TWO = false,
+          typename T, typename SlotFn, typename RowFn, typename QuadFn>
 __device__ __forceinline__ void walk_tile_async(const T *__restrict__ in, const int64_t *stride,
                                                 const int *box_lo, const int *box_len, int r0,
                                                 int r1, const TileShape &t, float4 *ring,
-                                                SlotFn slot_fn, RowFn row_fn, QuadFn quad_fn) {
+                                                SlotFn slot_fn, RowFn row_fn, QuadFn quad_fn,
+                                                const float *__restrict__ in2 = nullptr) {
     const int gl = threadIdx.x & (t.LPR - 1), grp = threadIdx.x / t.LPR;
     const int L = box_len[D - 1];
     const int nt = blockDim.x;
@@ -759,12 +763,16 @@ __device__ __forceinline__ void walk_tile_async(const T *__restrict__ in, const 
         it.next();
         return start - t.head + 4 * gl;
     };
+    const uint32_t ring2_off = 16u * uint32_t(ST * QMAX * nt);
     auto issue = [&](int stage) {
         int coords[kMaxDim];
         const int64_t a0 = row_addr(iss, coords);
 #pragma unroll
         for (int i = 0; i < QMAX; ++i)
-            if (FULL || ok[i]) cpq(slot_addr(stage, i), in + a0 + i * step);
+            if (FULL || ok[i]) {
+                cpq(slot_addr(stage, i), in + a0 + i * step);
+                if (TWO) cp_async16(slot_addr(stage, i) + ring2_off, in2 + a0 + i * step);
+            }
     };
 #pragma unroll
     for (int k = 0; k < ST - 1; ++k) {
@@ -784,7 +792,8 @@ __device__ __forceinline__ void walk_tile_async(const T *__restrict__ in, const 
         for (int i = 0; i < QMAX; ++i)
             if (FULL || ok[i]) {
                 const float4 v = ldsq<T>(slot_addr(stage_c, i));
-                quad_fn(st, sd[i], i, v, v, a0 + i * step);
+                const float4 v2 = TWO ? lds128(slot_addr(stage_c, i) + ring2_off) : v;
+                quad_fn(st, sd[i], i, v, v2, a0 + i * step);
             }
         stage_c = (stage_c + 1 == ST) ? 0 : stage_c + 1;
         stage_i = (stage_i + 1 == ST) ? 0 : stage_i + 1;

@@ -87,14 +87,22 @@ Tuning default_tuning(const Geom &g) {
     t.map_tma = (map_tma_box(g, bx, by, bz) && dl.b < 32) ? 1 : 0;
     t.map_flat = 0;
     t.hist_walk = 0;
-    int64_t bc = (int64_t(sms) * 4 + cells - 1) / cells;
-    bc = std::min<int64_t>(std::max<int64_t>(bc, 1), std::max<int64_t>(rows / 4, 1));
-    bc = std::min<int64_t>(bc, 32);
-    // the adjoint's integer accumulators hold at most 65535 voxels per chunk:
-    // ceil(rows / chunks) rows of b_last voxels (b_last <= 65535, checked by
-    // mclahe_plan)
+    // Backward chunks per cell: about one CTA per SM for one volume (the
+    // batched backward fills the GPU with the other volumes; every chunk
+    // restages its cell's tables and closes with block barriers, so fewer,
+    // longer chunks run faster), a power of two (a cell's rows -- a power of
+    // two times the walk's row groups for power-of-two kernels -- then split
+    // into whole row groups, so no warp idles at the closing barrier), and
+    // enough of them that the adjoint's integer accumulators hold at most
+    // 65535 voxels per chunk: ceil(rows / chunks) rows of b_last voxels
+    // (b_last <= 65535, checked by mclahe_plan).
+    const auto pow2_floor = [](int64_t v) { while (v & (v - 1)) v &= v - 1; return v; };
+    const auto pow2_ceil = [](int64_t v) { int64_t p = 1; while (p < v) p <<= 1; return p; };
     const int64_t rows_max = std::max<int64_t>(65535 / dl.b, 1);
-    bc = std::max<int64_t>(bc, (rows + rows_max - 1) / rows_max);
+    const int64_t bc_min = pow2_ceil((rows + rows_max - 1) / rows_max);
+    int64_t bc = pow2_floor(std::min<int64_t>(std::max<int64_t>((sms + cells - 1) / cells, 1),
+                                              std::max<int64_t>(rows / 4, 1)));
+    bc = std::max<int64_t>(std::min<int64_t>(bc, 32), bc_min);
     t.bwd_chunks = int(bc);
     return t;
 }

@@ -346,6 +346,32 @@ MCLAHE_API mclahe_status mclahe_backward(mclahe_plan_t plan, const float *d_in, 
                               float *d_grad_clip, mclahe_stream_t stream);
 
 /*
+ * mclahe_forward_host -- mclahe_forward_typed on n_vol volumes of one plan
+ * that live in host memory (no counterpart in the paper).  Volume v is copied
+ * host -> device into slot v mod 2, mapped on `stream`, and its output copied
+ * device -> host; the copies run on two library-owned streams, so the input
+ * copy of volume v + 1 and the output copy of volume v - 1 overlap the mapping
+ * of volume v.  The call returns once everything is enqueued; `stream` then
+ * waits for the last output copy (the host outputs are complete when `stream`
+ * is).
+ *   dtype          element type of the inputs (the outputs are float32).
+ *   h_in, h_out    host arrays of n_vol host pointers, prod(shape) elements
+ *                  each; page-locked memory lets the copies overlap (pageable
+ *                  memory works, serialised).  Outputs may repeat a pointer.
+ *   d_in, d_out, d_ws   two-element host arrays of device pointers: the two
+ *                  slots' input buffers (prod(shape) elements of dtype,
+ *                  16-byte aligned), output buffers (float32) and workspaces
+ *                  (ws_bytes each, zeroed once by the caller); all distinct.
+ *   d_clip         nullable device float [n_vol] clip limits.
+ * Argument errors return before anything is enqueued.  Calls from several host
+ * threads are serialised on the host.
+ */
+MCLAHE_API mclahe_status mclahe_forward_host(mclahe_plan_t plan, mclahe_dtype dtype, int n_vol,
+                                             const void *const *h_in, float *const *h_out,
+                                             void *const *d_in, float *const *d_out, void *const *d_ws,
+                                             size_t ws_bytes, const float *d_clip, mclahe_stream_t stream);
+
+/*
  * mclahe_forward_batch -- mclahe_forward on n_vol volumes of one plan, each
  * with its own workspace (which then serves mclahe_backward or
  * mclahe_backward_batch), on `branches` (1..16) parallel branches forked from

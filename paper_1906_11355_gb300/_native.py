@@ -31,7 +31,7 @@ MCLAHE_RANGE_ADAPTIVE = 1
 EXPORTS = (
     "mclahe_plan", "mclahe_plan_destroy", "mclahe_plan_query", "mclahe_workspace_bytes",
     "mclahe_forward", "mclahe_backward", "mclahe_backward_batch", "mclahe_forward_batch",
-    "mclahe_batch", "mclahe_batch_workspace_bytes",
+    "mclahe_forward_host", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
     "mclahe_plan_set_shapes", "mclahe_forward_graph", "mclahe_noalloc_sync_status",
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
         lib.mclahe_backward_batch.restype = ctypes.c_int
         lib.mclahe_forward_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, sz, vp, vp, ctypes.c_int]
         lib.mclahe_forward_batch.restype = ctypes.c_int
+        lib.mclahe_forward_host.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, sz, vp, vp]
+        lib.mclahe_forward_host.restype = ctypes.c_int
         lib.mclahe_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp), vp, sz, vp, vp, ctypes.c_int]
         lib.mclahe_batch.restype = ctypes.c_int
@@ -380,6 +382,18 @@ def mclahe_backward(plan, d_in, d_grad_out, d_ws, ws_bytes, d_clip, d_grad_lut, 
 def _ptr_array(items):
     arr = (ctypes.c_void_p * len(items))(*[_ptr(x) for x in items])
     return arr
+
+
+def mclahe_forward_host(plan, dtype, h_in, h_out, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None):
+    """mclahe_forward_typed on len(h_in) host-resident volumes through two
+    device slots (d_in, d_out, d_ws: two buffers each), copies overlapping."""
+    n = len(h_in)
+    if len(h_out) != n or len(d_in) != 2 or len(d_out) != 2 or len(d_ws) != 2:
+        raise ValueError("h_in and h_out of equal length; two device slots")
+    st = load().mclahe_forward_host(plan.handle, int(dtype), n, _ptr_array(h_in), _ptr_array(h_out),
+                                    _ptr_array(d_in), _ptr_array(d_out), _ptr_array(d_ws), int(ws_bytes),
+                                    _ptr(d_clip), _stream(stream))
+    _check(st, "mclahe_forward_host")
 
 
 def mclahe_forward_batch(plan, d_in, d_out, d_ws, ws_bytes, d_clip=None, stream=None, branches=8):

@@ -68,6 +68,38 @@ class MCLAHE:
 
     __call__ = forward
 
+    def forward_host(self, xs, outs=None, clip=None, stream=None):
+        """Run Algorithm 1 on volumes held in host memory (mclahe_forward_host):
+        xs is a list of CPU tensors of the plan's shape (float32, uint16 or
+        uint8, all the same dtype; page-locked memory lets the copies overlap
+        the kernels).  Returns the float32 CPU outputs (`outs`, or new
+        page-locked tensors); they are complete once `stream` (default: the
+        current stream) has reached this call's end.  Two device slots are kept
+        on the object for later calls."""
+        if not xs:
+            return [] if outs is None else outs
+        dt = xs[0].dtype
+        for x in xs:
+            if x.device.type != "cpu" or x.dtype != dt or not x.is_contiguous() or tuple(x.shape) != self.shape:
+                raise ValueError("expected contiguous CPU tensors of one dtype and the plan's shape")
+        if outs is None:
+            outs = [torch.empty(self.shape, dtype=torch.float32).pin_memory() for _ in xs]
+        if len(outs) != len(xs) or any(o.device.type != "cpu" or o.dtype != torch.float32 or
+                                       not o.is_contiguous() or tuple(o.shape) != self.shape for o in outs):
+            raise ValueError("outs: contiguous float32 CPU tensors of the plan's shape, one per input")
+        key = (dt, str(self.device))
+        slots = getattr(self, "_host_slots", None)
+        if slots is None or slots[0] != key:
+            d_in = [torch.empty(self.shape, dtype=dt, device=self.device) for _ in range(2)]
+            d_out = [torch.empty(self.shape, dtype=torch.float32, device=self.device) for _ in range(2)]
+            d_ws = [torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+            slots = (key, d_in, d_out, d_ws)
+            self._host_slots = slots
+        _, d_in, d_out, d_ws = slots
+        nat.mclahe_forward_host(self.plan, nat.dtype_code(xs[0]), xs, outs, d_in, d_out, d_ws, self.ws_bytes,
+                                clip, stream)
+        return outs
+
     def autotune(self, x, out=None, stream=None):
         """Pick launch shapes by timing candidates on x (overwrites out)."""
         self._check_volume(x)

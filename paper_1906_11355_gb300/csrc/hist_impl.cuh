@@ -273,10 +273,87 @@ __device__ __forceinline__ void warp_lut(const uint32_t *h, int nb, int LS, int6
     for (int j = nb + lane; j < LS; j += 32) out[j] = st.flat ? 0.0f : 1.0f;
 }
 
+// The tables of n kernels at once, g = nw / n >= 2 warps per kernel: kernel
+// i's histogram h0 + i P is built by warps [i g, (i + 1) g), lane li of the
+// group owning the contiguous bins [li c, li c + c), c = ceil(nb / 32 g).
+// The statistics are the same integers (the group's scan gives every lane the
+// same exclusive prefixes as a warp or block scan) and every entry the same
+// float operations as warp_lut's: the tables are identical.  All threads of
+// the block call it (two block barriers).
+__device__ __forceinline__ void group_luts(const uint32_t *h0, int P, int n, int nb, int LS, int64_t V,
+                                           float clip, float *__restrict__ lut, int64_t k0,
+                                           int64_t kstep) {
+    __shared__ uint32_t s_su[32], s_nc[32];
+    const unsigned full = 0xffffffffu;
+    const int nw = int(blockDim.x >> 5), warp = int(threadIdx.x >> 5), lane = int(threadIdx.x & 31);
+    const int g = nw / n, i = warp / g, wg = warp - i * g;
+    const bool active = i < n;   // the last nw - n g warps idle
+    const uint32_t *h = h0 + size_t(active ? i : 0) * P;
+    LutStats st;
+    clip_threshold(clip, V, st.tf, st.tr);
+    const int L = 32 * g, li = wg * 32 + lane;
+    const int per = (nb + L - 1) / L;
+    const int j0 = active ? min(li * per, nb) : nb, j1 = active ? min(j0 + per, nb) : nb;
+    uint32_t nc = 0, su = 0;
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const uint32_t v = h[j];
+        if (int64_t(v) > st.tf) nc += 1; else su += v;
+    }
+    uint32_t is = su, ia = nc;   // inclusive scans within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t xs = __shfl_up_sync(full, is, o);
+        const uint32_t xa = __shfl_up_sync(full, ia, o);
+        if (lane >= o) {
+            is += xs;
+            ia += xa;
+        }
+    }
+    if (lane == 31) {
+        s_su[warp] = is;
+        s_nc[warp] = ia;
+    }
+    __syncthreads();
+    uint32_t os = 0, oa = 0, ts = 0, ta = 0;   // earlier warps of the group; the group's totals
+    if (active)
+        for (int w = 0; w < g; ++w) {
+            const uint32_t a = s_su[i * g + w], b = s_nc[i * g + w];
+            if (w < wg) {
+                os += a;
+                oa += b;
+            }
+            ts += a;
+            ta += b;
+        }
+    __syncthreads();   // s_su / s_nc may be reused by the next call
+    if (!active) return;
+    st.S_tot = ts;
+    st.N_c = ta;
+    const uint32_t v0 = h[0];
+    st.S0 = (int64_t(v0) > st.tf) ? 0 : v0;
+    st.A0 = (int64_t(v0) > st.tf) ? 1 : 0;
+    const int64_t H_c = V - st.S_tot;
+    const float E = __fsub_rn(float(H_c - st.N_c * st.tf), __fmul_rn(float(st.N_c), st.tr));
+    st.Eb = __fdiv_rn(E, float(nb));
+    st.flat = (st.N_c == 0) && (st.S_tot == st.S0);
+    st.den = st.diff(st.S_tot, st.N_c, nb - 1);
+    float *out = lut + (k0 + i * kstep) * LS;
+    int64_t Sj = int64_t(os) + (is - su), Aj = int64_t(oa) + (ia - nc);   // exclusive prefixes at j0
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
+        const uint32_t v = h[j];
+        if (int64_t(v) > st.tf) Aj += 1; else Sj += v;
+        out[j] = st.flat ? 0.0f : __fdiv_rn(st.diff(Sj, Aj, j), st.den);
+    }
+    for (int j = nb + li; j < LS; j += L) out[j] = st.flat ? 0.0f : 1.0f;
+}
+
 // Tables of n kernels whose histograms lie in shared memory at h + i * P:
-// one block-wide build for a single kernel, else one warp per kernel (block
-// builds one kernel after another measured slower on the 4-D workload: 3
-// kernels per 512-thread CTA).
+// one block-wide build for a single kernel, a group of warps per kernel while
+// every kernel gets at least two warps, else one warp per kernel (block builds
+// one kernel after another measured slower on the 4-D workload: 3 kernels per
+// 512-thread CTA).
 __device__ __forceinline__ void build_luts(const uint32_t *h, int P, int n, int nb, int LS, int64_t V,
                                            float clip, float *__restrict__ lut, int64_t k0,
                                            int64_t kstep) {
@@ -285,6 +362,10 @@ __device__ __forceinline__ void build_luts(const uint32_t *h, int P, int n, int 
         return;
     }
     const int nw = int(blockDim.x >> 5), warp = int(threadIdx.x >> 5);
+    if (2 * n <= nw && nw <= 32) {
+        group_luts(h, P, n, nb, LS, V, clip, lut, k0, kstep);
+        return;
+    }
     for (int i = warp; i < n; i += nw)
         warp_lut(h + size_t(i) * P, nb, LS, V, clip, lut + (k0 + i * kstep) * LS);
 }

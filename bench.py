@@ -44,7 +44,9 @@ def pass_kernel(pass_name, info):
     """Kernel launched by a pass (for the roofline and the ncu launch list)."""
     flat = info["hist_shares"] > 0
     if pass_name == "range":
-        return "k_hist_flat" if (flat and info["mode"] == 1) else "k_range_global"
+        if info["mode"] == 1:
+            return "k_hist_flat" if flat else "k_range_kernels"
+        return "k_range_global"
     mapk = "k_map_tma" if info["map_tma"] else ("k_map_flat" if info["map_flat"] else "k_map")
     histk = "k_hist_flat" if flat else ("k_hist_staged" if info["hist_walk"] == 3 else "k_hist")
     return {"hist": histk, "map": mapk}[pass_name]
@@ -169,14 +171,16 @@ def algorithmic_bytes(info, adaptive, has_range):
     (a global range not given by the caller); the histogram pass reads the
     input once and writes the histograms, tables and ranges; the mapping pass
     reads the input and writes the output (4 B per voxel each).  With the
-    adaptive range the flat histogram form has a range pass of its own, which
-    reads the input once."""
+    adaptive range the flat histogram form, and the cluster form with the
+    separate streaming range sweep, have a range pass of their own, which
+    reads the input once and writes every kernel's min/max keys."""
     N = info["n_voxels"]
     K = info["n_kernels"]
     nb = info["n_bins"]
     ls = info["table_stride"]
-    if adaptive:   # the flat form's range pass writes every kernel's min/max keys
-        rng = 4 * N + 8 * K if info["hist_shares"] > 0 else 0
+    if adaptive:
+        own = info["hist_shares"] > 0 or (info.get("range_pass", 0) and info["hist_walk"] != 3)
+        rng = 4 * N + 8 * K if own else 0
     else:
         rng = 0 if has_range else 4 * N
     return {
@@ -203,7 +207,7 @@ def kernel_source_hash(pass_name):
 
 # launch shapes that select the kernel variant of a pass
 VARIANT_KEYS = {
-    "range": ("hist_shares", "hist_walk", "hist_threads"),
+    "range": ("hist_shares", "hist_walk", "hist_threads", "range_pass"),
     "hist": ("hist_group", "hist_cluster", "hist_copies", "hist_shares", "hist_walk", "hist_threads"),
     "map": ("map_chunks", "map_tma", "map_flat"),
 }
@@ -482,7 +486,7 @@ def measure_fwd_bwd(dev, steps, warmup):
 # native arm
 # ---------------------------------------------------------------------------
 SHAPE_KEYS = ("hist_group", "hist_cluster", "hist_shares", "hist_copies", "hist_walk", "hist_threads",
-              "map_flat", "map_chunks", "map_tma", "tuned")
+              "map_flat", "map_chunks", "map_tma", "range_pass", "tuned")
 
 
 class Workload:

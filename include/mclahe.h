@@ -125,10 +125,14 @@ typedef struct {
                                      not flat or not launched yet) */
     int32_t map_tma;              /* 1: the mapping pass streams its cells as TMA box tiles */
     int32_t hist_walk;            /* rows of the histogram pass: 0 cp.async ring, 1 TMA box
-                                     tiles, 2 per-thread loads (least shared memory) */
+                                     tiles, 2 per-thread loads (least shared memory), 3 the
+                                     kernel's footprint staged in the cluster's shared memory */
     int32_t hist_threads;         /* threads per histogram CTA (256; 512 allowed for 4-D) */
     int32_t map_flat;             /* 1: the mapping pass deals map_chunks shares per cell out to
                                      a persistent grid (per-thread walk only) */
+    int32_t range_pass;           /* 1 (adaptive range, cluster form, walks 0-2): the per-kernel
+                                     ranges come from a streaming sweep before the histogram
+                                     pass (mclahe_plan_set_range_pass) */
 } mclahe_plan_info;
 
 /*
@@ -489,7 +493,9 @@ MCLAHE_API mclahe_status mclahe_autotune(mclahe_plan_t plan, const float *d_in, 
  *   hist_walk     0: per-thread cp.async row ring; 1: TMA box tiles (2- to 4-D volumes
  *                 whose last extent is a multiple of 4, footprint rows of at most 256
  *                 elements per tile); 2: per-thread loads into registers (no row buffer
- *                 in shared memory).
+ *                 in shared memory); 3: the kernel's footprint staged whole in the
+ *                 shared memory of its cluster (hist_group 1, hist_shares 0, 256
+ *                 threads, where it fits).
  *   hist_threads  threads per histogram CTA: 256, or 512 for 4-D volumes.
  *   map_chunks    CTAs per inter-kernel cell in the mapping pass, 1..64.
  *   map_tma       0: per-thread loads and stores; 1: TMA box tiles (3- and 4-D volumes
@@ -505,6 +511,23 @@ MCLAHE_API mclahe_status mclahe_plan_set_shapes(mclahe_plan_t plan, int32_t hist
                                                 int32_t hist_shares, int32_t hist_walk,
                                                 int32_t hist_threads, int32_t map_chunks,
                                                 int32_t map_tma, int32_t map_flat);
+
+/*
+ * mclahe_plan_set_range_pass -- where an adaptive plan's per-kernel ranges
+ * (Sec. III.D) are taken (host only; no counterpart in the paper).
+ *   separate  1: one streaming sweep over the volume in memory order
+ *             (MCLAHE_PASS_RANGE) leaves every kernel's min and max, and the
+ *             histogram pass reads them (the cluster form with walks 0-2; the
+ *             volume is then read from L2 by the histogram pass when it fits
+ *             there); 0: each histogram work item sweeps its footprint for its
+ *             range before binning it.
+ * The result is the same either way.  Returns MCLAHE_ERR_INVALID_ARG for a
+ * value other than 0 or 1, and MCLAHE_ERR_UNSUPPORTED for 1 on a plan whose
+ * range is global, whose last extent is not a multiple of 4, or whose keys (8
+ * bytes per kernel) and quad table (4 bytes per 4 elements of the last extent)
+ * exceed 48 KiB.  Sets tuned = 2.
+ */
+MCLAHE_API mclahe_status mclahe_plan_set_range_pass(mclahe_plan_t plan, int32_t separate);
 
 /* Size of the library's built-in scratch array used by mclahe_forward_noalloc. */
 #define MCLAHE_NOALLOC_SCRATCH_BYTES (8u << 20)

@@ -34,7 +34,8 @@ EXPORTS = (
     "mclahe_forward_host", "mclahe_batch", "mclahe_batch_workspace_bytes",
     "mclahe_autotune", "mclahe_sync_status", "mclahe_status_string", "mclahe_version",
     "mclahe_forward_pass", "mclahe_pass_launches", "mclahe_forward_noalloc",
-    "mclahe_plan_set_shapes", "mclahe_forward_graph", "mclahe_noalloc_sync_status",
+    "mclahe_plan_set_shapes", "mclahe_plan_set_range_pass", "mclahe_forward_graph",
+    "mclahe_noalloc_sync_status",
     "mclahe_batch_set_wait", "mclahe_forward_typed", "mclahe_metrics",
     "mclahe_metrics_workspace_bytes", "mclahe_gaussian_weights", "mclahe_filter_gaussian",
     "mclahe_filter_median", "mclahe_forward_chunked", "mclahe_slab_rows", "mclahe_forward_slab",
@@ -68,6 +69,7 @@ class PlanInfo(ctypes.Structure):
         ("hist_shares", ctypes.c_int32), ("hist_ctas", ctypes.c_int32),
         ("map_tma", ctypes.c_int32), ("hist_walk", ctypes.c_int32),
         ("hist_threads", ctypes.c_int32), ("map_flat", ctypes.c_int32),
+        ("range_pass", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -169,6 +171,8 @@ def load(path: str = LIB_PATH):
         lib.mclahe_batch_set_wait.restype = ctypes.c_int
         lib.mclahe_plan_set_shapes.argtypes = [vp] + [ctypes.c_int32] * 9
         lib.mclahe_plan_set_shapes.restype = ctypes.c_int
+        lib.mclahe_plan_set_range_pass.argtypes = [vp, ctypes.c_int32]
+        lib.mclahe_plan_set_range_pass.restype = ctypes.c_int
         lib.mclahe_version.argtypes = []
         lib.mclahe_version.restype = ctypes.c_int
         _lib = lib
@@ -258,6 +262,10 @@ def mclahe_plan_set_shapes(plan, hist_group, hist_cluster, hist_copies, hist_sha
                                          int(hist_threads), int(map_chunks), int(map_tma),
                                          int(map_flat)),
            "mclahe_plan_set_shapes")
+
+
+def mclahe_plan_set_range_pass(plan, separate):
+    _check(load().mclahe_plan_set_range_pass(plan.handle, int(separate)), "mclahe_plan_set_range_pass")
 
 
 def mclahe_workspace_bytes(plan) -> int:

@@ -112,13 +112,17 @@ class MCLAHE:
         info = nat.mclahe_plan_query(self.plan)
         return {k: int(info[k]) for k in ("hist_group", "hist_cluster", "hist_copies",
                                           "hist_shares", "hist_walk", "hist_threads", "map_chunks",
-                                          "map_tma", "map_flat")}
+                                          "map_tma", "map_flat", "range_pass")}
 
     def set_shapes(self, hist_group, hist_cluster, hist_copies, hist_shares, map_chunks,
-                   map_tma=0, hist_walk=0, hist_threads=256, map_flat=0):
-        """Set launch shapes explicitly (e.g. from another process's autotune)."""
+                   map_tma=0, hist_walk=0, hist_threads=256, map_flat=0, range_pass=None):
+        """Set launch shapes explicitly (e.g. from another process's autotune);
+        range_pass (adaptive plans): 1 the separate streaming range sweep, 0 the
+        sweep inside the histogram pass, None leaves it as it is."""
         nat.mclahe_plan_set_shapes(self.plan, hist_group, hist_cluster, hist_copies, hist_shares,
                                    map_chunks, map_tma, hist_walk, hist_threads, map_flat)
+        if range_pass is not None and (range_pass or self.adaptive):
+            nat.mclahe_plan_set_range_pass(self.plan, range_pass)
 
     # views into the workspace left by the last forward call
     def _view(self, key, count, dtype):

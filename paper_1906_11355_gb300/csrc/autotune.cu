@@ -8,7 +8,8 @@
 // its range pass, under the adaptive range) x row walk: the cp.async ring or
 // TMA tiles (where the geometry allows); and the staged walk (one kernel per
 // cluster of C in {1, 2, 4, 8} CTAs, its footprint in shared memory, where it
-// fits).  Mapping pass: per-thread loads
+// fits); for an adaptive range, the cluster form with and without the separate
+// streaming range pass.  Mapping pass: per-thread loads
 // or TMA tiles (where the geometry allows) x CTAs per cell in {1, 2, 4, ...,
 // 64} (at most one row per CTA).  Each candidate runs twice
 // after one warm-up and keeps its faster time; results are cached per
@@ -109,8 +110,9 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
     for (int j = 0; j + 1 < p->g.D; ++j) item_rows *= p->g.d[j].b;
     // candidates: G x R x threads per CTA (512 only for 4-D) x walk x form
     struct Cand {
-        int G, R, th, walk, C, S;
+        int G, R, th, walk, C, S, rp;
     };
+    const bool rp_ok = range_pass_fits(p->g);
     std::vector<Cand> cands;
     for (int G : groups)
         for (int R = 2; R <= 32; R <<= 1)
@@ -120,15 +122,18 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
                 for (int walk = 0; walk < 3; ++walk) {
                     if (walk == 1 && !tma_ok) continue;
                     if (hist_smem_bytes(p->g, R, G, hist_walk_code(walk), th) > 200 * 1024) continue;
-                    for (int C = 1; C <= 8; C <<= 1) cands.push_back({G, R, th, walk, C, 0});
+                    for (int C = 1; C <= 8; C <<= 1) {
+                        cands.push_back({G, R, th, walk, C, 0, 0});
+                        if (rp_ok) cands.push_back({G, R, th, walk, C, 0, 1});
+                    }
                     for (int S = 1; S <= 256 && S <= item_rows; S <<= 1)
-                        cands.push_back({G, R, th, walk, 1, S});
+                        cands.push_back({G, R, th, walk, 1, S, 0});
                 }
             }
     // the staged walk: one kernel per cluster of 1..8 CTAs
     for (int R = 2; R <= 32; R <<= 1)
         for (int C = 1; C <= 8; C <<= 1)
-            if (hist_staged_fits(p->g, R, C, nullptr)) cands.push_back({1, R, 256, 3, C, 0});
+            if (hist_staged_fits(p->g, R, C, nullptr)) cands.push_back({1, R, 256, 3, C, 0, 0});
     for (const Cand &c : cands) {
         if (s != MCLAHE_OK) break;
         p->t.hist_group = c.G;
@@ -137,6 +142,7 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
         p->t.hist_walk = c.walk;
         p->t.hist_chunks = c.C;
         p->t.hist_shares = c.S;
+        p->t.range_pass = c.rp;
         const float ms = time_passes(*p, MCLAHE_PASS_CLEAR, MCLAHE_PASS_HIST, d_in, d_out, ws, st, e0, e1);
         if (ms < 0.0f) continue;   // e.g. a cluster shape the device cannot schedule
         if (ms < best_ms) {
@@ -147,6 +153,7 @@ extern "C" mclahe_status mclahe_autotune(mclahe_plan_t p, const float *d_in, flo
             best.hist_walk = c.walk;
             best.hist_chunks = c.C;
             best.hist_shares = c.S;
+            best.range_pass = c.rp;
         }
     }
     cudaGetLastError();   // clear a failed candidate's launch error

@@ -720,7 +720,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const T *__restrict__ 
     };
 
     // ---- phase 1 (adaptive range only): min/max of every kernel of the group
-    if (ADAPTIVE && MODE != kHistFlat) {
+    if (ADAPTIVE && MODE != kHistFlat && (MODE == kHistMinMax || kkeys == nullptr)) {
         auto key_min = [&](int kg, float v) { atomicMax(&s_keys[2 * kg], ~float_key(v)); };
         auto key_max = [&](int kg, float v) { atomicMax(&s_keys[2 * kg + 1], float_key(v)); };
         auto slow_elem = [&](int x, float v) {
@@ -850,7 +850,7 @@ __device__ __forceinline__ void hist_group(const Geom &g, const T *__restrict__ 
             s_nlo[kg] = -lo;
             s_sc[kg] = range_scale(lo, hi, nb);
         }
-    } else if (ADAPTIVE) {   // flat pass: the range pass left the per-kernel keys
+    } else if (ADAPTIVE) {   // a range pass (flat, or k_range_kernels) left the per-kernel keys
         for (int kg = threadIdx.x; kg < GK; kg += blockDim.x) {
             float lo, hi;
             keys_to_range(__ldcg(kkeys + 2 * (kfirst + kg)), __ldcg(kkeys + 2 * (kfirst + kg) + 1), lo, hi);

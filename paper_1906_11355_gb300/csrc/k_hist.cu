@@ -92,8 +92,11 @@ cudaError_t launch_hist(const mclahe_plan_s &p, const float *in, unsigned char *
 
 // Items [item0, item0 + nitems) of the cluster form with the cp.async row ring
 // (the plan's groups, clusters and copies; a flat plan runs as one-CTA clusters)
-cudaError_t launch_hist_items(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+cudaError_t launch_hist_items(const mclahe_plan_s &plan, const float *in, unsigned char *ws,
                               const float *d_clip, cudaStream_t st, int64_t item0, int64_t nitems) {
+    // slabs of rows: each footprint's range is swept inside the pass
+    mclahe_plan_s p = plan;
+    p.t.range_pass = 0;
     HistTmaArgs none;
     std::memset(&none.map, 0, sizeof(none.map));
     const bool a = p.g.mode == MCLAHE_RANGE_ADAPTIVE;

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistT
            const T *__restrict__ in, const uint32_t *__restrict__ keys,
            const float *__restrict__ d_clip, uint32_t *__restrict__ hist, float *__restrict__ lut,
            float *__restrict__ lo_out, float *__restrict__ scale_out, int G, int R,
-           uint32_t *status, int64_t item0) {
+           uint32_t *status, int64_t item0, uint32_t *__restrict__ kkeys) {
     extern __shared__ __align__(128) uint32_t sh[];
     __shared__ __align__(8) uint64_t s_tbar[kHistTmaStages];
     // items in reverse launch order: the first clusters take the volume's end,
@@ -49,8 +49,9 @@ __global__ void __launch_bounds__(D >= 4 ? 512 : 256, D >= 4 ? 1 : (HW == kHistT
         tr = tma_ring_init<kHistTmaStages>(s_tbar, hist_tma_stage0(sh, hist_smem_words(g.P, R, G)),
                                            status);
     const HistTma ht{&tmap, tbx, tby};
+    // kkeys (nullable): per-kernel ranges left by k_range_kernels
     hist_group<D, ADAPTIVE, kHistCluster, HW, T>(g, in, keys, d_clip, hist, lut, lo_out, scale_out,
-                                              item, G, R, sh, 0, 1, 1, nullptr, nullptr, &ht, &tr);
+                                              item, G, R, sh, 0, 1, 1, nullptr, kkeys, &ht, &tr);
 }
 
 // Flat forms: CTA b takes shares [total * b / grid, total * (b + 1) / grid)
@@ -121,7 +122,9 @@ static cudaError_t launch_hist_cluster(const mclahe_plan_s &p, const T *in, unsi
                               reinterpret_cast<float *>(ws + p.ws.lut),
                               reinterpret_cast<float *>(ws + p.ws.lo),
                               reinterpret_cast<float *>(ws + p.ws.scale), p.t.hist_group,
-                              p.t.hist_copies, reinterpret_cast<uint32_t *>(ws + p.ws.status), item0);
+                              p.t.hist_copies, reinterpret_cast<uint32_t *>(ws + p.ws.status), item0,
+                              ADAPTIVE && uses_range_pass(p) ? reinterpret_cast<uint32_t *>(ws + p.ws.keys) + 2
+                                                             : nullptr);
 }
 
 // One launch of a flat form: a persistent grid of as many CTAs as fit on the

@@ -88,6 +88,10 @@ struct Tuning {
                         // 3 the kernel's footprint staged in shared memory (one kernel per
                         // cluster, where hist_staged_fits allows)
     int bwd_chunks;     // CTAs per inter-kernel cell in the backward pass (fixed by the plan)
+    int range_pass;     // 1: an adaptive plan's per-kernel ranges come from k_range_kernels
+                        // (one streaming sweep) before a cluster-form histogram pass,
+                        // instead of a sweep of each footprint inside it (where
+                        // range_pass_fits allows)
 };
 
 // Workspace layout (byte offsets, kWsAlign aligned).
@@ -826,6 +830,16 @@ __device__ __forceinline__ float4 lds_f32x4(uint32_t addr) {
 // ---------------------------------------------------------------------------
 // Host-side launchers (one translation unit each)
 // ---------------------------------------------------------------------------
+// k_range.cu: the per-kernel ranges of an adaptive plan in one sweep
+bool range_pass_fits(const Geom &g);
+cudaError_t launch_range_kernels(const mclahe_plan_s &p, const float *in, unsigned char *ws,
+                                 cudaStream_t st);
+// whether a plan's histogram pass takes its adaptive ranges from that sweep
+// (the cluster form with a ring, TMA or per-thread walk)
+inline bool uses_range_pass(const mclahe_plan_s &p) {
+    return p.t.range_pass && p.g.mode == MCLAHE_RANGE_ADAPTIVE && p.t.hist_shares == 0 &&
+           p.t.hist_walk != 3 && range_pass_fits(p.g);
+}
 cudaError_t launch_range(const mclahe_plan_s &p, const float *in, unsigned char *ws,
                          cudaStream_t st);
 cudaError_t launch_hist(const mclahe_plan_s &p, const float *in, unsigned char *ws,

@@ -87,6 +87,9 @@ Tuning default_tuning(const Geom &g) {
     t.map_tma = (map_tma_box(g, bx, by, bz) && dl.b < 32) ? 1 : 0;
     t.map_flat = 0;
     t.hist_walk = 0;
+    // the separate range sweep is an autotuner candidate; on the 3-D
+    // fluorescence workload it measured slower than the in-pass sweep
+    t.range_pass = 0;
     // Backward chunks per cell: about one CTA per SM for one volume (the
     // batched backward fills the GPU with the other volumes; every chunk
     // restages its cell's tables and closes with block barriers, so fewer,
@@ -156,13 +159,15 @@ mclahe_status run_pass(const mclahe_plan_s &p, int pass, const float *in, float 
             if (p.t.hist_shares > 0)
                 e = cudaMemsetAsync(ws + p.ws.keys, 0,
                                     p.ws.hist + sizeof(uint32_t) * size_t(p.g.K) * p.g.nb - p.ws.keys, st);
+            else if (uses_range_pass(p))
+                e = cudaMemsetAsync(ws + p.ws.keys, 0, (2 + 2 * size_t(p.g.K)) * sizeof(uint32_t), st);
             else if (p.g.mode == MCLAHE_RANGE_GLOBAL && !p.g.has_range)
                 e = cudaMemsetAsync(ws + p.ws.keys, 0, 2 * sizeof(uint32_t), st);
             break;
         case MCLAHE_PASS_RANGE:
-            e = p.g.mode == MCLAHE_RANGE_ADAPTIVE && p.t.hist_shares > 0
-                    ? launch_hist_range(p, in, ws, st)
-                    : launch_range(p, in, ws, st);
+            e = p.g.mode == MCLAHE_RANGE_ADAPTIVE && p.t.hist_shares > 0 ? launch_hist_range(p, in, ws, st)
+                : uses_range_pass(p)                                    ? launch_range_kernels(p, in, ws, st)
+                                                                        : launch_range(p, in, ws, st);
             break;
         case MCLAHE_PASS_HIST: e = launch_hist(p, in, ws, d_clip, st); break;
         case MCLAHE_PASS_LUT: break;   // built by the histogram pass's clusters
@@ -313,6 +318,16 @@ mclahe_status mclahe_plan_query(mclahe_plan_t p, mclahe_plan_info *info) {
     info->map_chunks = p->t.map_chunks;
     info->bwd_chunks = p->t.bwd_chunks;
     info->tuned = p->tuned;
+    info->range_pass = p->t.range_pass;
+    return MCLAHE_OK;
+}
+
+mclahe_status mclahe_plan_set_range_pass(mclahe_plan_t p, int32_t separate) {
+    if (!p || (separate != 0 && separate != 1)) return MCLAHE_ERR_INVALID_ARG;
+    if (separate && !range_pass_fits(p->g)) return MCLAHE_ERR_UNSUPPORTED;
+    p->t.range_pass = separate;
+    p->tuned = 2;
+    batch_forget_plan(p);   // graphs captured with the old passes
     return MCLAHE_OK;
 }
 
@@ -389,7 +404,7 @@ int mclahe_pass_launches(mclahe_plan_t p, mclahe_pass pass) {
     if (!p) return 0;
     switch (pass) {
         case MCLAHE_PASS_RANGE:
-            if (p->g.mode == MCLAHE_RANGE_ADAPTIVE) return p->t.hist_shares > 0 ? 1 : 0;
+            if (p->g.mode == MCLAHE_RANGE_ADAPTIVE) return p->t.hist_shares > 0 || uses_range_pass(*p) ? 1 : 0;
             return p->g.has_range ? 0 : 1;
         case MCLAHE_PASS_HIST:
         case MCLAHE_PASS_MAP: return 1;

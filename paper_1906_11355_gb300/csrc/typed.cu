@@ -43,6 +43,7 @@ cudaError_t range_of(const mclahe_plan_s &p, const uint8_t *in, unsigned char *w
 // the counts.
 mclahe_plan_s ring_plan(const mclahe_plan_s &p) {
     mclahe_plan_s q = p;
+    q.t.range_pass = 0;   // integer volumes sweep each footprint's range inside the pass
     while (q.t.hist_copies > 1 &&
            hist_smem_bytes(q.g, q.t.hist_copies, q.t.hist_group, 1, q.t.hist_threads) > 220 * 1024)
         q.t.hist_copies >>= 1;

@@ -106,7 +106,26 @@ def test_set_shapes_validates_and_round_trips(nat):
     assert nat.mclahe_pass_launches(plan, nat.MCLAHE_PASS_RANGE) == 1
     nat.mclahe_plan_set_shapes(plan, 1, 4, 16, 0, 1)
     assert nat.mclahe_plan_query(plan)["hist_shares"] == 0
+    # the cluster form: the sweep inside the histogram pass (the default), or
+    # the separate streaming range sweep
+    assert nat.mclahe_plan_query(plan)["range_pass"] == 0
     assert nat.mclahe_pass_launches(plan, nat.MCLAHE_PASS_RANGE) == 0
+    nat.mclahe_plan_set_range_pass(plan, 1)
+    assert nat.mclahe_plan_query(plan)["range_pass"] == 1
+    assert nat.mclahe_pass_launches(plan, nat.MCLAHE_PASS_RANGE) == 1
+    nat.mclahe_plan_set_range_pass(plan, 0)
+    assert nat.mclahe_plan_query(plan)["range_pass"] == 0
+    assert nat.mclahe_pass_launches(plan, nat.MCLAHE_PASS_RANGE) == 0
+    with pytest.raises(nat.MclaheError) as e:
+        nat.mclahe_plan_set_range_pass(plan, 2)
+    assert e.value.status == nat.MCLAHE_ERR_INVALID_ARG
+    glob = nat.mclahe_plan((64, 64), (16, 16), 64, 0.1)   # a global range has no per-kernel ranges
+    assert nat.mclahe_plan_query(glob)["range_pass"] == 0
+    with pytest.raises(nat.MclaheError) as e:
+        nat.mclahe_plan_set_range_pass(glob, 1)
+    assert e.value.status == nat.MCLAHE_ERR_UNSUPPORTED
+    odd_last = nat.mclahe_plan((16, 30), (4, 6), 64, 0.1, nat.MCLAHE_RANGE_ADAPTIVE)   # 30 % 4 != 0
+    assert nat.mclahe_plan_query(odd_last)["range_pass"] == 0
     bad = [(0, 1, 8, 0, 1), (n_last + 1, 1, 8, 0, 1), (1, 3, 8, 0, 1), (1, 16, 8, 0, 1),
            (1, 1, 12, 0, 1), (1, 1, 64, 0, 1), (1, 2, 8, 4, 1), (1, 1, 8, -1, 1),
            (1, 1, 8, 4097, 1), (1, 1, 8, 0, 0), (1, 1, 8, 0, 65)]

@@ -6,8 +6,7 @@ The paper compares its results with four classic metrics (Sec. II; Tables I
 and II, Sec. IV): the mean squared error to the original data (MSE), the peak
 signal-to-noise ratio derived from it (PSNR), the standard deviation
 (root-mean-square contrast, STD) and the Shannon (grey-level) entropy (ENT).
-It does not print their formulas.  Readings taken here (each listed with the
-others in DESIGN.md):
+It does not print their formulas.  Readings taken here:
   - every volume is first normalised to [0, 1] by its own minimum and maximum
     (a constant volume becomes all zeros), since MCLAHE's output lies in
     [0, 1] and the tables compare it with the raw data;

@@ -1,6 +1,6 @@
 // tma_host.cu -- tensor maps (TMA descriptors) of float32 volumes, encoded
-// with the driver's cuTensorMapEncodeTiled reached through the runtime (the
-// library does not link libcuda).
+// with the CUDA driver API's cuTensorMapEncodeTiled, reached through the
+// runtime's entry-point lookup (the library does not link libcuda).
 #include "mclahe_internal.cuh"
 
 namespace mclahe {

@@ -89,11 +89,17 @@ mclahe_status forward_int(const mclahe_plan_s &p, const T *in, float *out, unsig
     }
     if (hist_of(p, in, ws, d_clip, st) != cudaSuccess) return MCLAHE_ERR_CUDA;
     // the per-cell mapping grid: a flat plan's shares per cell would each restage
-    // the corner tables, so about two CTAs per SM in all instead
+    // the corner tables, so at least about two CTAs per SM in all, and chunks of
+    // at most 64 Ki voxels of a cell (large 4-D cells: 4 chunks per cell measured
+    // 5 % faster than 1 on 128x128x256x32 uint8; 3-D unchanged)
     mclahe_plan_s q = p;
     if (q.t.map_flat || q.t.map_tma) {
         const int64_t cells = n_cells(q.g);
-        q.t.map_chunks = int(std::min<int64_t>(64, std::max<int64_t>(1, (2 * int64_t(device_sms()) + cells - 1) / cells)));
+        int64_t cell_vox = 1;
+        for (int j = 0; j < q.g.D; ++j) cell_vox *= q.g.d[j].b;
+        q.t.map_chunks = int(std::min<int64_t>(
+            64, std::max<int64_t>({int64_t(1), (2 * int64_t(device_sms()) + cells - 1) / cells,
+                                   (cell_vox + 65535) / 65536})));
         q.t.map_flat = 0;
         q.t.map_tma = 0;
     }
